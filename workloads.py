@@ -1,0 +1,171 @@
+"""Seeded synthetic workloads for the generalized-random-tree point solve.
+
+This module holds the problem descriptions and the seeded point sets only: no
+step of the method's arithmetic.  Both the CUDA path (through its binding) and
+the CPU oracle take their inputs from here; neither side imports the other.
+
+A problem is a plain dict:
+    dim, D, f_coef=[b_0..b_deg], u0=(kind, params), strategy "A"|"B",
+    lam, c_pot (Strategy A), q (Strategy B), arity_law "uniform"|"abs",
+    precision "fp32"|"fp64".
+A workload adds the points: x [n, dim], t [n], ntrees [n], K, L, M, seed.
+
+The five workloads below follow the paper's test problems and its
+probabilistic-domain-decomposition set-up (Sec. 2.4 Examples 1-3, Sec. 3):
+    kpp_1d     u_t = u_xx + u^2 - u (McKean's KPP case, Eq. KPP-1D), 1-D, FP64
+    sin_2d     u_t = 0.5 Lap u + sin(u) (sin as its degree-9 Taylor polynomial)
+    uneven_2d  u_t = Lap u + u^2 on PDD interface points, uneven tree budgets
+    pdd_3d     u_t = 0.1 Lap u + u - u^3 on the 9 interior planes of a 4x4x4 split
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def mean_arity(f_coef, arity_law: str, extra_linear: float = 0.0) -> float:
+    """E_p[k] of the branching law over the nonzero terms of f (+ c u)."""
+    terms = []
+    for k, b in enumerate(f_coef):
+        b = b + (extra_linear if k == 1 else 0.0)
+        if b != 0.0:
+            terms.append((k, abs(b)))
+    if not terms:
+        return 0.0
+    if arity_law == "abs":
+        s = sum(a for _, a in terms)
+        return sum(k * a for k, a in terms) / s
+    return sum(k for k, _ in terms) / len(terms)
+
+
+def default_q(f_coef, arity_law: str) -> float:
+    """Leaf probability giving a Galton-Watson mean offspring of 2/3.
+
+    The tree is a Galton-Watson process with mean offspring (1-q) E_p[k]; the
+    paper's admissibility bound (Sec. 2.3, Eqs. q and qgen) is the boundary
+    (1-q) E_p[k] = 1.  Choosing 2/3 gives q = 2/3 for binary trees, a value the
+    paper itself uses (Fig. 6).
+    """
+    m = mean_arity(f_coef, arity_law)
+    return 1.0 - 2.0 / (3.0 * m) if m > 0 else 0.5
+
+
+SIN9 = [0.0, 1.0, 0.0, -1.0 / 6.0, 0.0, 1.0 / 120.0, 0.0, -1.0 / 5040.0, 0.0, 1.0 / 362880.0]
+
+
+def problem_kpp_1d() -> dict:
+    return dict(dim=1, D=1.0, f_coef=[0.0, -1.0, 1.0], u0=("gauss", (0.5, 0.3, 1.0 / math.sqrt(2.0), 0.0)),
+                strategy="A", lam=1.0, c_pot=1.0, q=0.5, arity_law="uniform", precision="fp64")
+
+
+def problem_sin_2d() -> dict:
+    return dict(dim=2, D=0.5, f_coef=list(SIN9), u0=("gauss", (0.0, 1.2, 1.0, 0.0, 0.0)), strategy="B",
+                lam=1.0, c_pot=0.0, q=default_q(SIN9, "abs"), arity_law="abs", precision="fp32")
+
+
+def problem_uneven_2d() -> dict:
+    return dict(dim=2, D=1.0, f_coef=[0.0, 0.0, 1.0], u0=("cos_prod", (1.5, 0.5, 1.0, 1.0)), strategy="B",
+                lam=1.0, c_pot=0.0, q=2.0 / 3.0, arity_law="uniform", precision="fp32")
+
+
+def problem_pdd_3d() -> dict:
+    return dict(dim=3, D=0.1, f_coef=[0.0, 1.0, 0.0, -1.0], u0=("tanh_prod", (0.0, 1.0, 2.0, 2.0, 2.0)),
+                strategy="B", lam=1.0, c_pot=0.0, q=2.0 / 3.0, arity_law="uniform", precision="fp32")
+
+
+def workload_kpp_1d() -> dict:
+    x = np.linspace(-2.0, 2.0, 16).reshape(-1, 1)
+    n = x.shape[0]
+    return dict(name="kpp_1d", problem=problem_kpp_1d(), x=x, t=np.full(n, 0.5), ntrees=np.full(n, 10_000, np.uint64),
+                K=8, L=4, M=4, seed=0)
+
+
+def workload_sin_2d() -> dict:
+    g = np.linspace(-3.0, 3.0, 16)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    x = np.concatenate([xy, xy], axis=0)
+    t = np.concatenate([np.full(len(xy), 0.25), np.full(len(xy), 1.0)])
+    return dict(name="sin_2d", problem=problem_sin_2d(), x=x, t=t, ntrees=np.full(len(t), 100_000, np.uint64),
+                K=10, L=5, M=5, seed=0)
+
+
+def interface_segments_8x8() -> list:
+    """The 112 interior unit segments of the 8x8 unit-square split of [0,8]^2."""
+    segs = []
+    for i in range(1, 8):          # vertical interfaces x = i
+        for j in range(8):
+            segs.append(((float(i), float(j)), (float(i), float(j + 1))))
+    for j in range(1, 8):          # horizontal interfaces y = j
+        for i in range(8):
+            segs.append(((float(i), float(j)), (float(i + 1), float(j))))
+    return segs
+
+
+def workload_uneven_2d(seed: int = 0) -> dict:
+    rng = np.random.default_rng(seed)
+    segs = interface_segments_8x8()
+    pick = rng.choice(len(segs), size=64, replace=False)
+    pts = []
+    for s in sorted(pick):
+        (x0, y0), (x1, y1) = segs[s]
+        f = (np.arange(64) + 0.5) / 64.0
+        pts.append(np.stack([x0 + f * (x1 - x0), y0 + f * (y1 - y0)], axis=1))
+    x = np.concatenate(pts, axis=0)
+    n = x.shape[0]
+    t = rng.uniform(0.1, 2.0, size=n)
+    ntrees = np.exp(rng.uniform(math.log(1e3), math.log(1e6), size=n)).astype(np.uint64)
+    return dict(name="uneven_2d", problem=problem_uneven_2d(), x=x, t=t, ntrees=ntrees, K=16, L=8, M=8, seed=0)
+
+
+def workload_pdd_3d() -> dict:
+    c = (np.arange(32) + 0.5) / 8.0
+    A, B = np.meshgrid(c, c, indexing="ij")
+    a, b = A.ravel(), B.ravel()
+    pts = []
+    for axis in range(3):
+        for plane in (1.0, 2.0, 3.0):
+            p = np.empty((a.size, 3))
+            others = [i for i in range(3) if i != axis]
+            p[:, axis] = plane
+            p[:, others[0]] = a
+            p[:, others[1]] = b
+            pts.append(p)
+    x = np.concatenate(pts, axis=0)
+    n = x.shape[0]
+    return dict(name="pdd_3d", problem=problem_pdd_3d(), x=x, t=np.full(n, 1.0), ntrees=np.full(n, 100_000, np.uint64),
+                K=12, L=6, M=6, seed=0)
+
+
+WORKLOADS = {
+    "kpp_1d": workload_kpp_1d,
+    "sin_2d": workload_sin_2d,
+    "uneven_2d": workload_uneven_2d,
+    "pdd_3d": workload_pdd_3d,
+}
+
+
+def subsample(wl: dict, npoints: int, ntrees: int | None = None, stride: int | None = None) -> dict:
+    """A smaller copy of a workload: every `stride`-th point, optionally fewer trees per point.
+
+    Point indices of the subsample are its own 0..n-1; callers that want the
+    full workload's random streams pass point_base / index lists themselves.
+    """
+    n = wl["x"].shape[0]
+    if stride is None:
+        stride = max(1, n // max(npoints, 1))
+    idx = np.arange(0, n, stride)[:npoints]
+    out = dict(wl)
+    out["x"] = wl["x"][idx].copy()
+    out["t"] = wl["t"][idx].copy()
+    nt = wl["ntrees"][idx].copy()
+    if ntrees is not None:
+        nt = np.minimum(nt, np.uint64(ntrees)).astype(np.uint64)
+    out["ntrees"] = nt
+    out["index"] = idx
+    return out
+
+
+def random_points(rng: np.random.Generator, n: int, dim: int, lo: float = -3.0, hi: float = 3.0) -> np.ndarray:
+    return rng.uniform(lo, hi, size=(n, dim))
