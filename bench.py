@@ -1,0 +1,410 @@
+"""Benchmark of the generalized-random-tree point solve on GB300.
+
+Workload (N=1): sin_2d -- u_t = 0.5 Lap u + sin(u) in 2-D (sin as its degree-9
+Taylor polynomial, offspring k drawn with p_k ~ |b_k|, Strategy B), u0 =
+1.2 exp(-|x|^2/2), a 16x16 grid on [-3,3]^2 at t in {0.25, 1.0} (512 point
+solves), 1e5 trees per point, series order K = 10, FP64 Pade [5/5], FP32
+walk.  One step = one full point solve of that batch (walk + finalize) with
+the inputs resident in device memory; the L2 is flushed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grt|reference]
+Under torchrun (N > 1) every rank solves its own batch of 512 point solves
+(point streams keyed by rank * 512 + i): weak scaling, no collective on the
+data path; the timed region is bracketed by barriers and the max over ranks
+is taken.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "trees/s, points/s at 1e-5 rel vs oracle; p50/p99 served latency vs plain path"
+WORKLOAD = "sin_2d"
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT_GB300 = 152
+ISSUE_PER_SM_PER_CLK = 4 * 32   # 4 schedulers x 1 warp-instruction x 32 threads
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic instruction model of the node body (FP32 walk), per unit of work
+# ---------------------------------------------------------------------------
+def instruction_model(problem: dict, K: int) -> dict:
+    """Minimal thread-instructions the method needs per node / leaf / split / tree.
+
+    Node (every node): Philox4x32-10 = 10 rounds x (2 IMAD.WIDE + 2 LOP3) = 40
+    per call (1 call for d <= 2, 2 for d = 3); 2 per uniform word (shift-or,
+    add); Box-Muller pair = 8 (lg2, mul, rsqrt, mul, sin, cos, 2 mul); decision
+    1; segment = 4 + d (select, 2 mul, sqrt = rsqrt + mul, d FFMA); weight
+    multiply 1; node count 1.
+    Leaf: g(y) (gauss 3 + 2d, cos/tanh product 3d, logistic 5, const 0), leaf
+    factor 1, continue with the next sibling = d + 5 (frame loads, test,
+    update).
+    Split: term search 2 per finite threshold past the leaf's, tau(1-S) 2,
+    factor 3 (two table loads, mul), Ne check 2, child label 3, push d + 4.
+    Tree: start 8, record 2, refill 6.
+    """
+    d = int(problem["dim"])
+    kind = problem["u0"][0]
+    nterms = sum(1 for b in problem["f_coef"] if b != 0.0)
+    calls = 2 if d == 3 else 1
+    words = 3 + (2 if d == 3 else 0)
+    pairs = 2 if d == 3 else 1
+    node = 40 * calls + 2 * words + 8 * pairs + 1 + (4 + d) + 1 + 1
+    g = {"gauss": 3 + 2 * d, "cos_prod": 3 * d, "tanh_prod": 3 * d, "logistic": 5, "const": 0}[kind]
+    leaf = g + 1 + (d + 5)
+    split = 2 * max(nterms - 1, 0) + 2 + 3 + 2 + 3 + (d + 4)
+    tree = 16
+    return dict(node=node, leaf=leaf, split=split, tree=tree)
+
+
+def algorithmic_instructions(model: dict, nodes: int, splits: int, trees: int) -> float:
+    leaves = nodes - splits
+    return float(model["node"] * nodes + model["leaf"] * leaves + model["split"] * splits + model["tree"] * trees)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            bus = parts[1].lower()
+            if self.bus_id and not (bus.endswith(self.bus_id[-12:]) or self.bus_id.endswith(bus[-12:])):
+                continue
+            try:
+                self.samples.append(dict(t=time.time(), sm=float(parts[2]), sm_max=float(parts[3]),
+                                         hw=parts[6], hw_thermal=parts[7], sw_thermal=parts[8], sw_power=parts[9]))
+            except ValueError:
+                continue
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        inside = [s for s in self.samples if t0 <= s["t"] <= t1]
+        window = "timed region"
+        if len(inside) < 3:  # short timed region: take the samples nearest to it
+            inside = sorted(self.samples, key=lambda s: min(abs(s["t"] - t0), abs(s["t"] - t1)))[:5]
+            window = "nearest samples to a short timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        reasons = set()
+        for s in inside:
+            for key, name in (("hw", "hw_slowdown"), ("hw_thermal", "hw_thermal_slowdown"),
+                              ("sw_thermal", "sw_thermal_slowdown"), ("sw_power", "sw_power_cap")):
+                if s[key].lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s["sm"] for s in inside), "sm_max_mhz": max(s["sm_max"] for s in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arms
+# ---------------------------------------------------------------------------
+def oracle_sample(wl: dict, target_s: float, nthreads: int):
+    """Time the oracle on a bounded leading slice of the workload's points (all their trees)."""
+    import oracle
+
+    oracle.build()
+    n = wl["x"].shape[0]
+    probe = min(4, n)
+    t0 = time.perf_counter()
+    oracle.solve(wl["problem"], wl["x"][:probe], wl["t"][:probe], wl["ntrees"][:probe], wl["K"], wl["L"], wl["M"],
+                 wl["seed"], nthreads=min(nthreads, probe))
+    per_point_thread = (time.perf_counter() - t0) * min(nthreads, probe) / probe
+    npts = int(max(1, min(n, target_s * nthreads / max(per_point_thread, 1e-6))))
+    npts = max(min(npts, n), min(nthreads, n))
+    return npts
+
+
+def run_oracle(wl: dict, npts: int, nthreads: int):
+    import oracle
+
+    t0 = time.perf_counter()
+    r = oracle.solve(wl["problem"], wl["x"][:npts], wl["t"][:npts], wl["ntrees"][:npts], wl["K"], wl["L"], wl["M"],
+                     wl["seed"], nthreads=nthreads)
+    return time.perf_counter() - t0, r
+
+
+def reference_arm(args) -> int:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workloads.WORKLOADS[WORKLOAD]()
+    nthreads = os.cpu_count() or 1
+    per_step_s = float(os.environ.get("GRT_REFERENCE_STEP_S", "2.0"))
+    npts = oracle_sample(wl, per_step_s, nthreads)
+    trees = float(np.sum(wl["ntrees"][:npts]))
+    for _ in range(args.warmup):
+        run_oracle(wl, npts, nthreads)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = run_oracle(wl, npts, nthreads)
+        times.append(dt)
+    total = sum(times)
+    value = trees * args.steps / total
+    sample = f"first {npts} of {wl['x'].shape[0]} point solves of {WORKLOAD}, all 1e5 trees each, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "points_per_s": npts * args.steps / total,
+        "config": {"workload": f"{WORKLOAD} (FP64 CPU oracle, the build's own plain reference; no upstream code exists)",
+                   "points_per_step": npts, "trees_per_point": int(wl["ntrees"][0]), "K": wl["K"], "L": wl["L"],
+                   "M": wl["M"], "parallelism": f"{nthreads} host threads"},
+        "cpu_baseline": {"value": value, "unit": "trees/s", "cores": nthreads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_arm(args) -> int:
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2402_06491_gb300 as grt
+
+    wl = workloads.WORKLOADS[WORKLOAD]()
+    n, K, L, M = wl["x"].shape[0], wl["K"], wl["L"], wl["M"]
+    point_base = rank * n
+    trees_per_step = float(np.sum(wl["ntrees"]))
+    ctx = grt.grt_create(wl["problem"], local)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, L, M)
+    grt.grt_plan_set_timing(plan, True)
+    x = torch.from_numpy(wl["x"]).to(dev)
+    t = torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        grt.grt_plan_execute(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    stream.synchronize()
+    nodes, splits, pruned = grt.grt_plan_counters(plan)
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    sampler = ClockSampler(f"{bus:02x}" if isinstance(bus, int) else None)
+    sampler.start()
+    time.sleep(0.3)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    walk_ms, fin_ms = [], []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+        wm, fm = grt.grt_plan_timing(plan)
+        walk_ms.append(wm)
+        fin_ms.append(fm)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t_wall1 = time.time()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    time.sleep(0.3)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0 - 0.05, t_wall1 + 0.05)
+
+    # parity spot check of this run's output (rank 0's first points) is in the test suite; here the
+    # result must at least be finite
+    u_host = u.cpu().numpy()
+    finite = bool(np.all(np.isfinite(u_host)))
+
+    # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result
+    xh = torch.from_numpy(wl["x"]).pin_memory().numpy()
+    th = torch.from_numpy(wl["t"]).pin_memory().numpy()
+    nth = torch.from_numpy(wl["ntrees"].astype(np.int64)).pin_memory().numpy().view(np.uint64)
+    uh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    sth = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    out = {"u": uh, "status": sth}
+    for _ in range(max(args.warmup, 1)):
+        grt.grt_solve(ctx, xh, th, nth, K, L, M, wl["seed"], point_base, want_coef=False, want_se=False, out=out)
+    e2e_steps = max(args.steps, 1)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        grt.grt_solve(ctx, xh, th, nth, K, L, M, wl["seed"], point_base, want_coef=False, want_se=False, out=out)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_s = float(te.item())
+    same = bool(np.array_equal(uh, u_host))
+    h2d = xh.nbytes + th.nbytes
+    d2h = uh.nbytes + sth.nbytes
+
+    launches_per_step = grt.grt_plan_launches(plan)
+    plan.close()
+    ctx.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * trees_per_step * args.steps / (total_ms / 1e3)
+    points_per_s = world * n * args.steps / (total_ms / 1e3)
+    model = instruction_model(wl["problem"], K)
+    inst = algorithmic_instructions(model, nodes, splits, int(trees_per_step))
+    walk_avg_ms = float(np.mean(walk_ms))
+    achieved = inst / (walk_avg_ms / 1e3) / 1e12
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT_GB300 * ISSUE_PER_SM_PER_CLK * sm_max * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "points_per_s": points_per_s,
+        "config": {
+            "workload": "sin_2d: 2-D u_t = 0.5 Lap u + sin u (degree-9 Taylor, p_k ~ |b_k|, Strategy B), "
+                        "u0 = 1.2 exp(-|x|^2/2), 16x16 grid on [-3,3]^2 x t in {0.25, 1}, 1e5 trees/point, "
+                        "K = 10, FP64 Pade [5/5], FP32 walk",
+            "points": n, "trees_per_point": int(wl["ntrees"][0]), "K": K, "L": L, "M": M,
+            "q": round(wl["problem"]["q"], 6), "seed": wl["seed"],
+            "l2": "flushed between steps (256 MiB device write, outside the timed events)",
+            "parallelism": f"{world} GPU(s), points sharded per rank (weak), no data-path collective",
+        },
+        "roofline": {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": "walk_kernel<float,2,B> (persistent tree walk)",
+            "work": f"{inst:.4g} algorithmic thread-instructions per launch = {model['node']}/node x {nodes} nodes"
+                    f" + {model['leaf']}/leaf x {nodes - splits} + {model['split']}/split x {splits}"
+                    f" + {model['tree']}/tree x {int(trees_per_step)}",
+            "walk_ms": walk_avg_ms, "finalize_ms": float(np.mean(fin_ms)),
+            "peak_basis": f"{SM_COUNT_GB300} SMs x 4 issue slots/clk x 32 threads x {sm_max:.0f} MHz (max SM clock)",
+        },
+        "e2e": {"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps, "matches_device_run": same},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
+        "finite_output": finite,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        target = float(os.environ.get("GRT_CPU_BASELINE_S", "15"))
+        npts = oracle_sample(wl, target, nthreads)
+        dt, _ = run_oracle(wl, npts, nthreads)
+        line["cpu_baseline"] = {"value": float(np.sum(wl["ntrees"][:npts])) / dt, "unit": "trees/s", "cores": nthreads,
+                                "kind": "oracle",
+                                "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each), "
+                                          f"{dt:.1f} s wall on {nthreads} threads"}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

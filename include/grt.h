@@ -1,0 +1,193 @@
+/*
+ * grt.h -- C ABI of libgrt, the GB300 (sm_103a) point solver for semilinear
+ * parabolic PDEs by generalized random trees and Pade resummation
+ * (Acebron & Rodriguez-Rozas, arXiv 2402.06491).
+ *
+ * Problem (Sec. 1, Eq. nonlinear_new, with L = D * Laplacian):
+ *     u_t = D Lap(u) + f(u),  x in R^d,  t > 0,     u(x, 0) = u0(x),
+ *     f(u) = sum_{k=0}^{deg} b_k u^k.
+ * A point solve estimates u(x_i, t_i) from N_i random trees per point:
+ *   - each tree is a branching Brownian motion (Sec. 2.1 algorithm, Fig. 1)
+ *     generated by Strategy A (exponential clock, Eqs. probexp1-probexp2) or
+ *     Strategy B (coin xi + uniform split time, Eqs. totalduhamel_B,
+ *     probexpB1, probexpBclosed);
+ *   - its weight (the multiplicative functional of Eqs. rep_strategyB /
+ *     probexpBclosed) is binned by its number of splitting events Ne into the
+ *     coefficient a_Ne of a possibly divergent series, trees with Ne > K being
+ *     pruned (Sec. 2.4);
+ *   - the series is summed by an [L/M] Pade approximant at eps = 1
+ *     (Sec. 2.1 end, Sec. 2.4), in FP64.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *     key = (seed mod 2^32, seed >> 32),
+ *     ctr = (lo32(id), hi32(id), tree | sub << 31, point_base + i),
+ * where id is the node's path label (root 0, child j of id is 16 id + j + 1).
+ * Results therefore depend only on (problem, point_base + i, x_i, t_i, N_i,
+ * K, L, M, seed) -- not on batching, scheduling or other points in the call.
+ *
+ * Conventions for every call:
+ *   - return value 0 (GRT_OK) or a negative GRT_E* code; the reason is kept
+ *     in the context and returned by grt_last_error();
+ *   - the caller owns every array passed in; the library never keeps a
+ *     pointer to a caller array after the call returns (grt_plan_execute
+ *     excepted: it reads and writes the device arrays asynchronously on the
+ *     given stream until that stream reaches the end of the call's work);
+ *   - a context and its plans are not thread-safe: use one per host thread;
+ *   - arrays are row-major; x holds n rows of dim doubles.
+ */
+#ifndef GRT_H
+#define GRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRT_MAX_DIM 3
+#define GRT_MAX_DEG 15
+#define GRT_MAX_K 16
+#define GRT_MAX_TREES_PER_POINT 2147483647ull
+
+/* Return codes. */
+#define GRT_OK 0
+#define GRT_EINVAL (-1)   /* an argument is outside its documented range     */
+#define GRT_ENOMEM (-2)   /* device or pinned host memory could not be had   */
+#define GRT_EDEVICE (-3)  /* a CUDA call failed (no device, launch error...) */
+#define GRT_ETIMEOUT (-4) /* a bounded device wait ran out                   */
+#define GRT_ENOTSUP (-5)  /* valid request this build does not support       */
+
+/* Strategy (Sec. 2.1 / Sec. 2.2). */
+#define GRT_STRATEGY_A 0
+#define GRT_STRATEGY_B 1
+
+/* Branching law over the nonzero terms b_k of F (A) or f (B). */
+#define GRT_ARITY_UNIFORM 0  /* p_k uniform: the paper's choice (Sec. 2.1 after Eq. probexp2) */
+#define GRT_ARITY_ABS_COEF 1 /* p_k proportional to |b_k|, weight b_k / p_k                 */
+
+/* Arithmetic of the tree walk (the Pade always runs in FP64). */
+#define GRT_FP32 0
+#define GRT_FP64 1
+
+/* Initial data u0 = g (parameters p[0..7]). */
+#define GRT_U0_CONST 0     /* p0                                              */
+#define GRT_U0_GAUSS 1     /* p0 + p1 exp(-|x - (p3,p4,p5)|^2 / (2 p2^2))     */
+#define GRT_U0_COS_PROD 2  /* p0 + p1 prod_i cos(p[2+i] x_i)                  */
+#define GRT_U0_TANH_PROD 3 /* p0 + p1 prod_i tanh(x_i - p[2+i])               */
+#define GRT_U0_LOGISTIC 4  /* p0 + p1 / (1 + exp(-(x_0 - p2) / p3))           */
+
+/* Per-point status bits. */
+#define GRT_STATUS_PADE_SINGULAR 1  /* a Pade pivot was below 1e-14 of the largest matrix
+                                       entry: the type was lowered [L-1/M-1] until solvable */
+#define GRT_STATUS_PADE_POLE_NEAR 2 /* |Q(1)| < 1e-8                                   */
+#define GRT_STATUS_SERIES_PARTIAL 4 /* fewer trees than requested contributed          */
+#define GRT_STATUS_HIGH_PRUNE 8     /* more than 1% of the trees had Ne > K            */
+
+/* Problem description (copied by grt_create). */
+typedef struct grt_problem {
+    int32_t dim;                       /* d in {1, 2, 3}                                      */
+    double D;                          /* diffusion constant >= 0 (variance 2 D tau per axis) */
+    int32_t f_deg;                     /* 0 <= deg <= GRT_MAX_DEG                             */
+    double f_coef[GRT_MAX_DEG + 1];    /* b_0 .. b_deg; entries above deg are ignored         */
+    int32_t u0_kind;                   /* GRT_U0_*                                            */
+    double u0_param[8];
+    int32_t strategy;                  /* GRT_STRATEGY_A | GRT_STRATEGY_B                     */
+    double lambda;                     /* A: clock rate lambda > 0                            */
+    double c_pot;                      /* A: potential c pulled out of f, F(u) = f(u) + c u   */
+    double q;                          /* B: leaf probability, 0 < q < 1                      */
+    int32_t arity_law;                 /* GRT_ARITY_*                                         */
+    int32_t precision;                 /* GRT_FP32 | GRT_FP64 (walk arithmetic)               */
+} grt_problem;
+
+typedef struct grt_ctx grt_ctx;
+typedef struct grt_plan grt_plan;
+
+/* Create a context for one problem on CUDA device `device`.
+ * Validates the problem (dim, deg, D >= 0, lambda > 0 for A, 0 < q < 1 for B,
+ * u0 kind, precision), builds the branching-law tables (Sec. 2.1 Eq. probexp2,
+ * Sec. 2.2 Eq. probexpB1) and selects the kernels.  On GRT_EINVAL/GRT_EDEVICE
+ * *out is set to NULL and no context exists (grt_last_error(NULL) then gives
+ * the reason of the last failed create in this thread). */
+int grt_create(const grt_problem *pb, int device, grt_ctx **out);
+
+/* Release the context, its cached device buffers and its stream.  Plans made
+ * from it must be destroyed first.  NULL is ignored. */
+void grt_destroy(grt_ctx *ctx);
+
+/* Text of the last error on this context (or of the last failed grt_create in
+ * this thread when ctx is NULL).  Owned by the library; valid until the next
+ * call on the same context. */
+const char *grt_last_error(const grt_ctx *ctx);
+
+/* Synchronous point solve with HOST arrays (the boundary of Sec. 3's
+ * "probabilistic part": interface values at single points).
+ *   n          number of points, 0 <= n < 2^31 (n = 0 returns GRT_OK at once)
+ *   x          [n][dim] positions; t [n] times >= 0; ntrees [n] trees per point,
+ *              0 <= N_i <= GRT_MAX_TREES_PER_POINT
+ *   K, L, M    series order 0 <= K <= GRT_MAX_K; Pade type with L, M >= 0, L + M <= K
+ *   seed       Philox key; point_base: global index of point 0 (for sharding:
+ *              the stream of point i is keyed by point_base + i < 2^32)
+ *   u_out      [n] Pade value; coef_out / se_out [n][K+1] coefficients a_n and
+ *              their standard errors (either may be NULL); status_out [n] bits
+ *              (may be NULL).
+ * Copies the inputs to the device, runs the walk and the FP64 finalize, and
+ * copies the results back before returning. */
+int grt_solve(grt_ctx *ctx, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K,
+              int L, int M, uint64_t seed, uint64_t point_base, double *u_out, double *coef_out,
+              double *se_out, int32_t *status_out);
+
+/* Device-resident form, for callers that keep their points in device memory
+ * and launch many solves of the same shape (e.g. under a CUDA graph).
+ * grt_plan_create fixes n, the per-point tree budgets (HOST array, copied) and
+ * K, L, M, lays out the (point, tree-tile) work items and allocates every
+ * device buffer the solve needs; grt_plan_execute then allocates nothing. */
+int grt_plan_create(grt_ctx *ctx, int64_t n, const uint64_t *ntrees, int K, int L, int M, grt_plan **out);
+
+/* Enqueue one solve on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * d_x [n][dim], d_t [n] are DEVICE arrays (t must be finite and >= 0: it is not
+ * checked here); d_u [n], d_coef / d_se [n][K+1] (may be NULL), d_status [n]
+ * (may be NULL) are DEVICE outputs.  Returns after enqueueing; launch errors
+ * are reported, results are ready when the stream reaches them.  Executions of
+ * one plan must not overlap in time (they share the plan's work buffers). */
+int grt_plan_execute(grt_plan *plan, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                     double *d_u, double *d_coef, double *d_se, int32_t *d_status, void *stream);
+
+/* Work counters of the plan's last execution (synchronises with it), summed
+ * over all points: nodes visited, splitting events (internal nodes, counting
+ * the split that prunes a tree) and trees pruned (Ne > K).  Any output may
+ * be NULL. */
+int grt_plan_counters(grt_plan *plan, uint64_t *nodes, uint64_t *splits, uint64_t *pruned);
+
+/* Kernel timing: when enabled (on != 0), every grt_plan_execute records CUDA
+ * events on its stream around the walk kernel and the finalize kernel.
+ * grt_plan_timing waits for the last execution's events and returns the two
+ * durations in milliseconds (GRT_EINVAL if timing was off for it). */
+int grt_plan_set_timing(grt_plan *plan, int on);
+int grt_plan_timing(grt_plan *plan, float *walk_ms, float *finalize_ms);
+
+/* Number of kernel launches one grt_plan_execute enqueues. */
+int grt_plan_launches(const grt_plan *plan);
+
+/* Release a plan.  NULL is ignored. */
+void grt_plan_destroy(grt_plan *plan);
+
+/* The FP64 [L/M] Pade stage alone (Sec. 2.1 end, Sec. 2.4), on the GPU, for
+ * n series given on the HOST as coef [n][K+1] (K >= L + M).  Writes u_out [n]
+ * and status_out [n] (may be NULL; only the PADE_* bits are set). */
+int grt_pade(grt_ctx *ctx, int64_t n, int K, int L, int M, const double *coef, double *u_out,
+             int32_t *status_out);
+
+/* Per-tree records for trees [first_tree, first_tree + ntrees) of one point,
+ * generated on the GPU with the context's walk arithmetic (HOST arrays):
+ * order [ntrees] (Ne, or K+1 when pruned), w [ntrees] tree weight (0 when
+ * pruned), nodes [ntrees] nodes visited, hash [ntrees] FNV-1a-64 over the node
+ * codes (0 leaf, term index + 1 split) in preorder.  Any output may be NULL.
+ * A diagnostic of the same streams the point solve uses (Sec. 2.2, Fig. 2). */
+int grt_trees(grt_ctx *ctx, const double *x, double t, uint64_t point_index, uint64_t first_tree, uint64_t ntrees,
+              int K, uint64_t seed, int32_t *order, double *w, uint32_t *nodes, uint64_t *hash);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRT_H */

@@ -1,0 +1,324 @@
+"""ctypes binding of libgrt (include/grt.h): argument marshalling only.
+
+Every step of a solve runs in the library's CUDA kernels; this module only
+converts Python/numpy/torch arguments to the C ABI and raises on errors.
+There is no CPU fallback: if libgrt.so is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrt.so")
+
+MAX_DIM = 3
+MAX_DEG = 15
+MAX_K = 16
+
+OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5
+STRATEGY = {"A": 0, "B": 1}
+ARITY_LAW = {"uniform": 0, "abs": 1}
+PRECISION = {"fp32": 0, "fp64": 1}
+U0_KIND = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4}
+STATUS_PADE_SINGULAR, STATUS_PADE_POLE_NEAR, STATUS_SERIES_PARTIAL, STATUS_HIGH_PRUNE = 1, 2, 4, 8
+
+
+class GrtError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"libgrt error {code}: {message}")
+        self.code = code
+
+
+class grt_problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("D", ctypes.c_double),
+        ("f_deg", ctypes.c_int32),
+        ("f_coef", ctypes.c_double * (MAX_DEG + 1)),
+        ("u0_kind", ctypes.c_int32),
+        ("u0_param", ctypes.c_double * 8),
+        ("strategy", ctypes.c_int32),
+        ("lambda_", ctypes.c_double),
+        ("c_pot", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("arity_law", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgrt.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    i64, u64, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+    f64p, u64p, i32p, u32p = _P(ctypes.c_double), _P(ctypes.c_uint64), _P(ctypes.c_int32), _P(ctypes.c_uint32)
+    sig = {
+        "grt_create": ([_P(grt_problem), i32, _P(_vp)], i32),
+        "grt_destroy": ([_vp], None),
+        "grt_last_error": ([_vp], ctypes.c_char_p),
+        "grt_solve": ([_vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, f64p, f64p, f64p, i32p], i32),
+        "grt_plan_create": ([_vp, i64, u64p, i32, i32, i32, _P(_vp)], i32),
+        "grt_plan_execute": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
+        "grt_plan_counters": ([_vp, u64p, u64p, u64p], i32),
+        "grt_plan_set_timing": ([_vp, i32], i32),
+        "grt_plan_timing": ([_vp, _P(ctypes.c_float), _P(ctypes.c_float)], i32),
+        "grt_plan_launches": ([_vp], i32),
+        "grt_plan_destroy": ([_vp], None),
+        "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
+        "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(_P(ctype))
+
+
+def _devptr(obj):
+    """A device address from a torch tensor, an int or None."""
+    if obj is None:
+        return None
+    if hasattr(obj, "data_ptr"):
+        return obj.data_ptr()
+    return int(obj)
+
+
+def problem_struct(pb: dict) -> grt_problem:
+    """Marshal a problem dict (see workloads.py) into the C struct."""
+    s = grt_problem()
+    s.dim = int(pb["dim"])
+    s.D = float(pb["D"])
+    fc = [float(v) for v in pb["f_coef"]]
+    if len(fc) > MAX_DEG + 1:
+        raise ValueError("f degree above 15")
+    s.f_deg = max(len(fc) - 1, 0)
+    for i, v in enumerate(fc):
+        s.f_coef[i] = v
+    kind, params = pb["u0"]
+    s.u0_kind = U0_KIND[kind]
+    for i, v in enumerate(params):
+        s.u0_param[i] = float(v)
+    s.strategy = STRATEGY[pb["strategy"]]
+    s.lambda_ = float(pb.get("lam", 1.0))
+    s.c_pot = float(pb.get("c_pot", 0.0))
+    s.q = float(pb.get("q", 0.5))
+    s.arity_law = ARITY_LAW[pb.get("arity_law", "uniform")]
+    s.precision = PRECISION[pb.get("precision", "fp32")]
+    return s
+
+
+class Context:
+    """A libgrt context (grt_ctx) for one problem on one device."""
+
+    def __init__(self, handle, problem: dict):
+        self._h = handle
+        self.problem = dict(problem)
+        self.dim = int(problem["dim"])
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            _load().grt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Plan:
+    """A libgrt plan (grt_plan): fixed points budgets and K, L, M; device-resident execution."""
+
+    def __init__(self, handle, ctx: Context, n: int, K: int, L: int, M: int, ntrees):
+        self._h = handle
+        self.ctx = ctx
+        self.n, self.K, self.L, self.M = n, K, L, M
+        self.ntrees = np.array(ntrees, dtype=np.uint64)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            _load().grt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check(rc: int, ctx_handle=None):
+    if rc != OK:
+        msg = _load().grt_last_error(ctx_handle)
+        raise GrtError(rc, msg.decode() if msg else "")
+
+
+def grt_last_error(ctx: Context | None) -> str:
+    msg = _load().grt_last_error(ctx.handle if ctx is not None else None)
+    return msg.decode() if msg else ""
+
+
+def grt_create(problem: dict, device: int = 0) -> Context:
+    lib = _load()
+    s = problem_struct(problem)
+    h = _vp()
+    _check(lib.grt_create(ctypes.byref(s), int(device), ctypes.byref(h)), None)
+    return Context(h.value, problem)
+
+
+def grt_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def grt_solve(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int, point_base: int = 0,
+              want_coef: bool = True, want_se: bool = True, want_status: bool = True, out: dict | None = None) -> dict:
+    """Synchronous point solve with host arrays. Returns u [n], coef/se [n, K+1], status [n]."""
+    lib = _load()
+    d = ctx.dim
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
+    n = xs.shape[0]
+    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
+    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    if out is None:
+        out = {}
+    u = out.get("u")
+    if u is None:
+        u = np.empty(n, np.float64)
+    coef = out.get("coef") if want_coef else None
+    if want_coef and coef is None:
+        coef = np.empty((n, K + 1), np.float64)
+    se = out.get("se") if want_se else None
+    if want_se and se is None:
+        se = np.empty((n, K + 1), np.float64)
+    st = out.get("status") if want_status else None
+    if want_status and st is None:
+        st = np.empty(n, np.int32)
+    rc = lib.grt_solve(ctx.handle, n, _ptr(xs, ctypes.c_double), _ptr(ts, ctypes.c_double),
+                       _ptr(nt, ctypes.c_uint64), K, L, M, int(seed), int(point_base), _ptr(u, ctypes.c_double),
+                       _ptr(coef, ctypes.c_double), _ptr(se, ctypes.c_double), _ptr(st, ctypes.c_int32))
+    _check(rc, ctx.handle)
+    return dict(u=u, coef=coef, se=se, status=st)
+
+
+def grt_plan_create(ctx: Context, ntrees, K: int, L: int, M: int) -> Plan:
+    lib = _load()
+    nt = np.ascontiguousarray(np.asarray(ntrees, np.uint64).reshape(-1))
+    h = _vp()
+    _check(lib.grt_plan_create(ctx.handle, nt.size, _ptr(nt, ctypes.c_uint64), K, L, M, ctypes.byref(h)), ctx.handle)
+    return Plan(h.value, ctx, nt.size, K, L, M, nt)
+
+
+def grt_plan_execute(plan: Plan, x, t, seed: int, point_base: int, u, coef=None, se=None, status=None,
+                     stream=None) -> None:
+    """Enqueue a solve on `stream` (torch.cuda.Stream, a raw handle, or None).
+
+    x, t, u, coef, se, status are device buffers: torch CUDA tensors (float64 /
+    int32, contiguous) or raw device addresses.
+    """
+    lib = _load()
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.grt_plan_execute(plan.handle, _devptr(x), _devptr(t), int(seed), int(point_base), _devptr(u),
+                              _devptr(coef), _devptr(se), _devptr(status), sh)
+    _check(rc, plan.ctx.handle)
+
+
+def grt_plan_counters(plan: Plan):
+    """(nodes visited, splitting events, trees pruned) of the plan's last execution."""
+    lib = _load()
+    a, b, c = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib.grt_plan_counters(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), plan.ctx.handle)
+    return int(a.value), int(b.value), int(c.value)
+
+
+def grt_plan_set_timing(plan: Plan, on: bool) -> None:
+    _check(_load().grt_plan_set_timing(plan.handle, 1 if on else 0), plan.ctx.handle)
+
+
+def grt_plan_timing(plan: Plan):
+    """(walk kernel ms, finalize kernel ms) of the last execution, from CUDA events on its stream."""
+    a, b = ctypes.c_float(0), ctypes.c_float(0)
+    _check(_load().grt_plan_timing(plan.handle, ctypes.byref(a), ctypes.byref(b)), plan.ctx.handle)
+    return float(a.value), float(b.value)
+
+
+def grt_plan_launches(plan: Plan) -> int:
+    return int(_load().grt_plan_launches(plan.handle))
+
+
+def grt_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def grt_pade(ctx: Context, coef, L: int, M: int):
+    """FP64 [L/M] Pade at eps = 1 of each row of coef [n, K+1], on the GPU. Returns (u, status)."""
+    lib = _load()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    if c.ndim == 1:
+        c = c.reshape(1, -1)
+    n, K1 = c.shape
+    u = np.empty(n, np.float64)
+    st = np.empty(n, np.int32)
+    _check(lib.grt_pade(ctx.handle, n, K1 - 1, L, M, _ptr(c, ctypes.c_double), _ptr(u, ctypes.c_double),
+                        _ptr(st, ctypes.c_int32)), ctx.handle)
+    return u, st
+
+
+def grt_trees(ctx: Context, x, t: float, point_index: int, first_tree: int, ntrees: int, K: int, seed: int) -> dict:
+    """Per-tree records (order, weight, nodes, topology hash) of one point's trees, from the GPU."""
+    lib = _load()
+    xs = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
+    order = np.empty(ntrees, np.int32)
+    w = np.empty(ntrees, np.float64)
+    nodes = np.empty(ntrees, np.uint32)
+    h = np.empty(ntrees, np.uint64)
+    _check(lib.grt_trees(ctx.handle, _ptr(xs, ctypes.c_double), float(t), int(point_index), int(first_tree),
+                         int(ntrees), K, int(seed), _ptr(order, ctypes.c_int32), _ptr(w, ctypes.c_double),
+                         _ptr(nodes, ctypes.c_uint32), _ptr(h, ctypes.c_uint64)), ctx.handle)
+    return dict(order=order, w=w, nodes=nodes, hash=h)
+
+
+EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
+            "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
+            "grt_pade", "grt_trees"]

@@ -1,0 +1,628 @@
+// grt_api.cu -- the C ABI of libgrt (declared in include/grt.h).
+//
+// Host work only: argument validation, the branching-law tables, the
+// (point, tree-tile) work layout, device buffers, and the launches of the
+// walk and finalize kernels.  Every step of the solve itself runs on the GPU.
+#include "grt.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "grt_device.cuh"
+#include "grt_launch.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && ptr) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+      ptr = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+  }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+// Threshold of a cumulative probability on the 32-bit word scale:
+// round-to-nearest of 2^32 * cum, clamped to [0, 2^32].
+uint64_t word_threshold(double cum) {
+  const double v = cum * 4294967296.0;
+  if (v <= 0.0) return 0;
+  if (v >= 4294967296.0) return 4294967296ull;
+  return (uint64_t)llround(v);
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+struct grt_plan;
+
+struct grt_ctx {
+  grt_problem pb{};
+  int device = 0;
+  int num_sms = 0;
+  grt::WalkParams base{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  grt_plan *solve_plan = nullptr;
+  DevBuf dx, dt, du, dcoef, dse, dstatus;
+  int set_error(int code, const std::string &msg) {
+    err = msg;
+    return code;
+  }
+  int cuda_error(cudaError_t e, const char *where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return GRT_EDEVICE;
+  }
+};
+
+struct grt_plan {
+  grt_ctx *ctx = nullptr;
+  int64_t n = 0;
+  int K = 0, L = 0, M = 0;
+  uint32_t total_items = 0;
+  uint64_t total_trees = 0;
+  std::vector<uint64_t> host_ntrees;
+  DevBuf prefix, ntrees, part, cnt, counter, nodes_pt, pruned_pt, splits_pt;
+  cudaStream_t last_stream = nullptr;
+  int launches = 0;
+  bool timing = false, timed_last = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  void release() {
+    for (auto &e : ev)
+      if (e) {
+        cudaEventDestroy(e);
+        e = nullptr;
+      }
+    splits_pt.release();
+    prefix.release();
+    ntrees.release();
+    part.release();
+    cnt.release();
+    counter.release();
+    nodes_pt.release();
+    pruned_pt.release();
+  }
+};
+
+namespace {
+
+#define GRT_CUDA(ctx, expr)                                        \
+  do {                                                             \
+    cudaError_t e_ = (expr);                                       \
+    if (e_ != cudaSuccess) return (ctx)->cuda_error(e_, #expr);    \
+  } while (0)
+
+// Validate the problem and build the walk's tables (branching law of
+// Sec. 2.1 Eq. probexp2 / Sec. 2.2 Eq. probexpB1 on 32-bit thresholds).
+int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
+  if (pb.dim < 1 || pb.dim > GRT_MAX_DIM) return why = "dim must be 1, 2 or 3", GRT_EINVAL;
+  if (!is_finite(pb.D) || pb.D < 0.0) return why = "D must be finite and >= 0", GRT_EINVAL;
+  if (pb.f_deg < 0 || pb.f_deg > GRT_MAX_DEG) return why = "f_deg must be in [0, 15]", GRT_EINVAL;
+  for (int k = 0; k <= pb.f_deg; ++k)
+    if (!is_finite(pb.f_coef[k])) return why = "f_coef must be finite", GRT_EINVAL;
+  if (pb.u0_kind < GRT_U0_CONST || pb.u0_kind > GRT_U0_LOGISTIC) return why = "unknown u0_kind", GRT_EINVAL;
+  for (int i = 0; i < 8; ++i)
+    if (!is_finite(pb.u0_param[i])) return why = "u0_param must be finite", GRT_EINVAL;
+  if (pb.u0_kind == GRT_U0_GAUSS && pb.u0_param[2] == 0.0) return why = "GAUSS width p2 must be nonzero", GRT_EINVAL;
+  if (pb.u0_kind == GRT_U0_LOGISTIC && pb.u0_param[3] == 0.0)
+    return why = "LOGISTIC width p3 must be nonzero", GRT_EINVAL;
+  if (pb.strategy != GRT_STRATEGY_A && pb.strategy != GRT_STRATEGY_B) return why = "unknown strategy", GRT_EINVAL;
+  if (pb.arity_law != GRT_ARITY_UNIFORM && pb.arity_law != GRT_ARITY_ABS_COEF)
+    return why = "unknown arity_law", GRT_EINVAL;
+  if (pb.precision != GRT_FP32 && pb.precision != GRT_FP64) return why = "unknown precision", GRT_EINVAL;
+  const bool A = pb.strategy == GRT_STRATEGY_A;
+  if (A && !(is_finite(pb.lambda) && pb.lambda > 0.0)) return why = "Strategy A needs lambda > 0", GRT_EINVAL;
+  if (A && !is_finite(pb.c_pot)) return why = "c_pot must be finite", GRT_EINVAL;
+  if (!A && !(pb.q > 0.0 && pb.q < 1.0)) return why = "Strategy B needs 0 < q < 1", GRT_EINVAL;
+
+  // Terms: the nonzero coefficients of F = f + c u (A) or f (B), by ascending power.
+  const int deg = (A && pb.f_deg < 1) ? 1 : pb.f_deg;
+  double F[GRT_MAX_DEG + 1];
+  for (int k = 0; k <= deg; ++k) F[k] = (k <= pb.f_deg ? pb.f_coef[k] : 0.0) + ((A && k == 1) ? pb.c_pot : 0.0);
+  int nt = 0;
+  double coef[grt::kMaxTerms];
+  for (int k = 0; k <= deg; ++k) {
+    if (F[k] != 0.0) {
+      w.arity[nt] = k;
+      coef[nt] = F[k];
+      ++nt;
+    }
+  }
+  w.nterms = nt;
+  for (int i = nt; i < grt::kMaxTerms; ++i) {
+    w.arity[i] = 0;
+    w.term_factor[i] = 0.0;
+  }
+  double prob[grt::kMaxTerms];
+  double sabs = 0.0;
+  for (int i = 0; i < nt; ++i) sabs += std::fabs(coef[i]);
+  for (int i = 0; i < nt; ++i)
+    prob[i] = pb.arity_law == GRT_ARITY_ABS_COEF ? std::fabs(coef[i]) / sabs : 1.0 / (double)nt;
+
+  uint64_t T[grt::kMaxTerms + 1];
+  int ncat = 0;
+  if (!A) {
+    // joint draw over {leaf, term 1..nt}: P(leaf) = q, P(term i) = (1 - q) p_i
+    if (nt == 0) {
+      T[0] = 4294967296ull;
+      ncat = 1;
+      w.leaf_factor = 1.0;
+    } else {
+      T[0] = word_threshold(pb.q);
+      double cp = 0.0;
+      for (int i = 0; i < nt; ++i) {
+        cp += prob[i];
+        T[i + 1] = word_threshold(pb.q + (1.0 - pb.q) * cp);
+      }
+      T[nt] = 4294967296ull;
+      ncat = nt + 1;
+      if (T[0] == 0) return why = "q too small for a 32-bit leaf threshold", GRT_EINVAL;
+      w.leaf_factor = 4294967296.0 / (double)T[0];
+      for (int i = 0; i < nt; ++i) {
+        const double P = (double)(T[i + 1] - T[i]) / 4294967296.0;
+        w.term_factor[i] = P > 0.0 ? coef[i] / P : 0.0;
+      }
+    }
+  } else {
+    w.leaf_factor = 1.0;
+    if (nt > 0) {
+      double cp = 0.0;
+      for (int i = 0; i < nt; ++i) {
+        cp += prob[i];
+        T[i] = word_threshold(cp);
+      }
+      T[nt - 1] = 4294967296ull;
+      ncat = nt;
+      for (int i = 0; i < nt; ++i) {
+        const double P = (double)(T[i] - (i == 0 ? 0ull : T[i - 1])) / 4294967296.0;
+        w.term_factor[i] = P > 0.0 ? coef[i] / (pb.lambda * P) : 0.0;
+      }
+    }
+  }
+  // finite thresholds: all before the first that reaches 2^32
+  int nfin = 0;
+  while (nfin < ncat - 1 && T[nfin] < 4294967296ull) ++nfin;
+  w.ncat_thr = nfin;
+  for (int j = 0; j <= grt::kMaxTerms; ++j) w.thr[j] = j < nfin ? (uint32_t)T[j] : 0xFFFFFFFFu;
+
+  // problem scalars
+  w.u0_kind = pb.u0_kind;
+  w.two_D = 2.0 * pb.D;
+  w.inv_lambda = A ? 1.0 / pb.lambda : 1.0;
+  w.lam_minus_c = A ? pb.lambda - pb.c_pot : 0.0;
+  w.two_Df = (float)w.two_D;
+  w.inv_lambdaf = (float)w.inv_lambda;
+  w.lam_minus_cf = (float)w.lam_minus_c;
+  const double *a = pb.u0_param;
+  double c[8] = {a[0], a[1], 0, 0, 0, 0, 0, 0};
+  switch (pb.u0_kind) {
+  case GRT_U0_GAUSS:
+    c[2] = -1.0 / (2.0 * a[2] * a[2]);
+    c[3] = a[3];
+    c[4] = a[4];
+    c[5] = a[5];
+    break;
+  case GRT_U0_COS_PROD:
+  case GRT_U0_TANH_PROD:
+    c[2] = a[2];
+    c[3] = a[3];
+    c[4] = a[4];
+    break;
+  case GRT_U0_LOGISTIC:
+    c[2] = a[2];
+    c[3] = -1.0 / a[3];
+    break;
+  default:
+    break;
+  }
+  for (int i = 0; i < 8; ++i) {
+    w.u0d[i] = c[i];
+    w.u0f[i] = (float)c[i];
+  }
+  return GRT_OK;
+}
+
+void set_round_keys(grt::WalkParams &w, uint64_t seed) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    w.rk0[r] = k0;
+    w.rk1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+size_t acc_size(const grt_ctx *c) { return c->pb.precision == GRT_FP64 ? sizeof(double) : sizeof(float); }
+
+// Lay out the work items of a plan and size its buffers (grow only).
+int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L, int M) {
+  grt_ctx *c = p->ctx;
+  if (n < 0 || n > 0x7FFFFFFFll) return c->set_error(GRT_EINVAL, "n must be in [0, 2^31)");
+  if (K < 0 || K > GRT_MAX_K) return c->set_error(GRT_EINVAL, "K must be in [0, 16]");
+  if (L < 0 || M < 0 || L + M > K) return c->set_error(GRT_EINVAL, "need L, M >= 0 and L + M <= K");
+  if (n > 0 && !ntrees) return c->set_error(GRT_EINVAL, "ntrees is NULL");
+  const bool same = p->n == n && p->K == K && p->host_ntrees.size() == (size_t)n &&
+                    (n == 0 || std::memcmp(p->host_ntrees.data(), ntrees, (size_t)n * sizeof(uint64_t)) == 0);
+  p->K = K;
+  p->L = L;
+  p->M = M;
+  if (same && p->prefix.ptr) return GRT_OK;
+  std::vector<uint32_t> prefix((size_t)n + 1), nt32((size_t)n);
+  uint64_t items = 0, trees = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
+    prefix[(size_t)i] = (uint32_t)items;
+    items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
+    trees += ntrees[i];
+    nt32[(size_t)i] = (uint32_t)ntrees[i];
+    if (items >= 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "too many work items (total trees too large)");
+  }
+  prefix[(size_t)n] = (uint32_t)items;
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  GRT_CUDA(c, p->prefix.ensure(prefix.size() * sizeof(uint32_t)));
+  GRT_CUDA(c, p->ntrees.ensure(nt32.size() * sizeof(uint32_t) + 4));
+  GRT_CUDA(c, p->part.ensure((size_t)items * 3 * (K + 1) * acc_size(c) + 16));
+  GRT_CUDA(c, p->cnt.ensure((size_t)items * (K + 3) * sizeof(uint32_t) + 16));
+  GRT_CUDA(c, p->counter.ensure(sizeof(uint32_t)));
+  GRT_CUDA(c, p->nodes_pt.ensure((size_t)n * 8 + 8));
+  GRT_CUDA(c, p->pruned_pt.ensure((size_t)n * 8 + 8));
+  GRT_CUDA(c, p->splits_pt.ensure((size_t)n * 8 + 8));
+  GRT_CUDA(c, cudaMemcpy(p->prefix.ptr, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  if (n > 0)
+    GRT_CUDA(c, cudaMemcpy(p->ntrees.ptr, nt32.data(), nt32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  GRT_CUDA(c, cudaMemset(p->counter.ptr, 0, sizeof(uint32_t)));
+  p->n = n;
+  p->total_items = (uint32_t)items;
+  p->total_trees = trees;
+  p->host_ntrees.assign(ntrees, ntrees + n);
+  p->launches = items > 0 ? 2 : 1;
+  return GRT_OK;
+}
+
+int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base, double *d_u,
+                 double *d_coef, double *d_se, int32_t *d_status, cudaStream_t stream) {
+  grt_ctx *c = p->ctx;
+  if (p->n == 0) return GRT_OK;
+  if (!d_x || !d_t || !d_u) return c->set_error(GRT_EINVAL, "x, t and u must be non-NULL");
+  if (point_base + (uint64_t)p->n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  grt::WalkParams w = c->base;
+  set_round_keys(w, seed);
+  w.K = p->K;
+  w.point_base = (uint32_t)point_base;
+  w.x = d_x;
+  w.t = d_t;
+  w.ntrees = p->ntrees.as<uint32_t>();
+  w.prefix = p->prefix.as<uint32_t>();
+  w.n = (int)p->n;
+  w.total_items = p->total_items;
+  w.part = p->part.ptr;
+  w.cnt = p->cnt.as<uint32_t>();
+  w.counter = p->counter.as<uint32_t>();
+  const bool fp64 = c->pb.precision == GRT_FP64;
+  if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[0], stream));
+  if (p->total_items > 0) {
+    GRT_CUDA(c, cudaMemsetAsync(p->counter.ptr, 0, sizeof(uint32_t), stream));
+    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
+  }
+  if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[1], stream));
+  grt::FinalizeParams f{};
+  f.part = p->part.ptr;
+  f.cnt = p->cnt.as<uint32_t>();
+  f.prefix = p->prefix.as<uint32_t>();
+  f.ntrees = p->ntrees.as<uint32_t>();
+  f.n = (int)p->n;
+  f.K = p->K;
+  f.L = p->L;
+  f.M = p->M;
+  f.u = d_u;
+  f.coef = d_coef;
+  f.se = d_se;
+  f.status = d_status;
+  f.nodes_pt = p->nodes_pt.as<unsigned long long>();
+  f.pruned_pt = p->pruned_pt.as<unsigned long long>();
+  f.splits_pt = p->splits_pt.as<unsigned long long>();
+  f.counter = p->counter.as<uint32_t>();
+  GRT_CUDA(c, grt::launch_finalize(fp64, f, stream));
+  if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[2], stream));
+  p->timed_last = p->timing;
+  p->last_stream = stream;
+  return GRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grt_create(const grt_problem *pb, int device, grt_ctx **out) {
+  if (!out) return GRT_EINVAL;
+  *out = nullptr;
+  if (!pb) {
+    g_create_error = "problem is NULL";
+    return GRT_EINVAL;
+  }
+  grt::WalkParams w{};
+  std::string why;
+  int rc = build_tables(*pb, w, why);
+  if (rc != GRT_OK) {
+    g_create_error = why;
+    return rc;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return GRT_EDEVICE;
+  }
+  if (device < 0 || device >= ndev) {
+    g_create_error = "device index out of range";
+    return GRT_EINVAL;
+  }
+  grt_ctx *c = new (std::nothrow) grt_ctx();
+  if (!c) {
+    g_create_error = "out of host memory";
+    return GRT_ENOMEM;
+  }
+  c->pb = *pb;
+  c->device = device;
+  c->base = w;
+  if ((e = cudaSetDevice(device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    g_create_error = std::string("CUDA set-up failed: ") + cudaGetErrorString(e);
+    delete c;
+    return GRT_EDEVICE;
+  }
+  *out = c;
+  return GRT_OK;
+}
+
+void grt_destroy(grt_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->solve_plan) {
+    ctx->solve_plan->release();
+    delete ctx->solve_plan;
+  }
+  ctx->dx.release();
+  ctx->dt.release();
+  ctx->du.release();
+  ctx->dcoef.release();
+  ctx->dse.release();
+  ctx->dstatus.release();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *grt_last_error(const grt_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int grt_solve(grt_ctx *c, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K, int L, int M,
+              uint64_t seed, uint64_t point_base, double *u_out, double *coef_out, double *se_out,
+              int32_t *status_out) {
+  if (!c) return GRT_EINVAL;
+  if (n < 0) return c->set_error(GRT_EINVAL, "n must be >= 0");
+  if (n == 0) return GRT_OK;
+  if (!x || !t || !ntrees || !u_out) return c->set_error(GRT_EINVAL, "x, t, ntrees and u_out must be non-NULL");
+  if (point_base + (uint64_t)n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
+  const int dim = c->pb.dim;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(is_finite(t[i]) && t[i] >= 0.0)) return c->set_error(GRT_EINVAL, "t must be finite and >= 0");
+    for (int d = 0; d < dim; ++d)
+      if (!is_finite(x[i * dim + d])) return c->set_error(GRT_EINVAL, "x must be finite");
+  }
+  if (!c->solve_plan) {
+    c->solve_plan = new (std::nothrow) grt_plan();
+    if (!c->solve_plan) return c->set_error(GRT_ENOMEM, "out of host memory");
+    c->solve_plan->ctx = c;
+  }
+  int rc = plan_configure(c->solve_plan, n, ntrees, K, L, M);
+  if (rc != GRT_OK) return rc;
+  GRT_CUDA(c, c->dx.ensure((size_t)n * dim * sizeof(double)));
+  GRT_CUDA(c, c->dt.ensure((size_t)n * sizeof(double)));
+  GRT_CUDA(c, c->du.ensure((size_t)n * sizeof(double)));
+  if (coef_out) GRT_CUDA(c, c->dcoef.ensure((size_t)n * (K + 1) * sizeof(double)));
+  if (se_out) GRT_CUDA(c, c->dse.ensure((size_t)n * (K + 1) * sizeof(double)));
+  if (status_out) GRT_CUDA(c, c->dstatus.ensure((size_t)n * sizeof(int32_t)));
+  cudaStream_t s = c->stream;
+  GRT_CUDA(c, cudaMemcpyAsync(c->dx.ptr, x, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
+  GRT_CUDA(c, cudaMemcpyAsync(c->dt.ptr, t, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+  rc = plan_execute(c->solve_plan, c->dx.as<double>(), c->dt.as<double>(), seed, point_base, c->du.as<double>(),
+                    coef_out ? c->dcoef.as<double>() : nullptr, se_out ? c->dse.as<double>() : nullptr,
+                    status_out ? c->dstatus.as<int32_t>() : nullptr, s);
+  if (rc != GRT_OK) return rc;
+  GRT_CUDA(c, cudaMemcpyAsync(u_out, c->du.ptr, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (coef_out)
+    GRT_CUDA(c, cudaMemcpyAsync(coef_out, c->dcoef.ptr, (size_t)n * (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (se_out)
+    GRT_CUDA(c, cudaMemcpyAsync(se_out, c->dse.ptr, (size_t)n * (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (status_out)
+    GRT_CUDA(c, cudaMemcpyAsync(status_out, c->dstatus.ptr, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GRT_CUDA(c, cudaStreamSynchronize(s));
+  return GRT_OK;
+}
+
+int grt_plan_create(grt_ctx *c, int64_t n, const uint64_t *ntrees, int K, int L, int M, grt_plan **out) {
+  if (!c || !out) return GRT_EINVAL;
+  *out = nullptr;
+  grt_plan *p = new (std::nothrow) grt_plan();
+  if (!p) return c->set_error(GRT_ENOMEM, "out of host memory");
+  p->ctx = c;
+  p->n = -1;
+  int rc = plan_configure(p, n, ntrees, K, L, M);
+  if (rc != GRT_OK) {
+    p->release();
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return GRT_OK;
+}
+
+int grt_plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                     double *d_u, double *d_coef, double *d_se, int32_t *d_status, void *stream) {
+  if (!p) return GRT_EINVAL;
+  return plan_execute(p, d_x, d_t, seed, point_base, d_u, d_coef, d_se, d_status, (cudaStream_t)stream);
+}
+
+int grt_plan_counters(grt_plan *p, uint64_t *nodes, uint64_t *splits, uint64_t *pruned) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  uint64_t sn = 0, ss = 0, sp = 0;
+  if (p->n > 0) {
+    GRT_CUDA(c, cudaSetDevice(c->device));
+    GRT_CUDA(c, cudaStreamSynchronize(p->last_stream));
+    std::vector<uint64_t> a((size_t)p->n), b((size_t)p->n), d((size_t)p->n);
+    GRT_CUDA(c, cudaMemcpy(a.data(), p->nodes_pt.ptr, a.size() * 8, cudaMemcpyDeviceToHost));
+    GRT_CUDA(c, cudaMemcpy(b.data(), p->pruned_pt.ptr, b.size() * 8, cudaMemcpyDeviceToHost));
+    GRT_CUDA(c, cudaMemcpy(d.data(), p->splits_pt.ptr, d.size() * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < a.size(); ++i) {
+      sn += a[i];
+      sp += b[i];
+      ss += d[i];
+    }
+  }
+  if (nodes) *nodes = sn;
+  if (splits) *splits = ss;
+  if (pruned) *pruned = sp;
+  return GRT_OK;
+}
+
+int grt_plan_set_timing(grt_plan *p, int on) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (on) {
+    GRT_CUDA(c, cudaSetDevice(c->device));
+    for (auto &e : p->ev)
+      if (!e) GRT_CUDA(c, cudaEventCreate(&e));
+  }
+  p->timing = on != 0;
+  return GRT_OK;
+}
+
+int grt_plan_timing(grt_plan *p, float *walk_ms, float *finalize_ms) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (!p->timed_last) return c->set_error(GRT_EINVAL, "timing was not enabled for the last execution");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  GRT_CUDA(c, cudaEventSynchronize(p->ev[2]));
+  float a = 0.f, b = 0.f;
+  GRT_CUDA(c, cudaEventElapsedTime(&a, p->ev[0], p->ev[1]));
+  GRT_CUDA(c, cudaEventElapsedTime(&b, p->ev[1], p->ev[2]));
+  if (walk_ms) *walk_ms = a;
+  if (finalize_ms) *finalize_ms = b;
+  return GRT_OK;
+}
+
+int grt_plan_launches(const grt_plan *p) { return p ? p->launches : 0; }
+
+void grt_plan_destroy(grt_plan *p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  p->release();
+  delete p;
+}
+
+int grt_pade(grt_ctx *c, int64_t n, int K, int L, int M, const double *coef, double *u_out, int32_t *status_out) {
+  if (!c) return GRT_EINVAL;
+  if (n < 0 || n > 0x7FFFFFFFll) return c->set_error(GRT_EINVAL, "n must be in [0, 2^31)");
+  if (K < 0 || K > GRT_MAX_K || L < 0 || M < 0 || L + M > K)
+    return c->set_error(GRT_EINVAL, "need 0 <= K <= 16, L, M >= 0, L + M <= K");
+  if (n == 0) return GRT_OK;
+  if (!coef || !u_out) return c->set_error(GRT_EINVAL, "coef and u_out must be non-NULL");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  DevBuf dc, du, ds;
+  auto cleanup = [&]() {
+    dc.release();
+    du.release();
+    ds.release();
+  };
+  cudaError_t e;
+  if ((e = dc.ensure((size_t)n * (K + 1) * 8)) != cudaSuccess || (e = du.ensure((size_t)n * 8)) != cudaSuccess ||
+      (e = ds.ensure((size_t)n * 4)) != cudaSuccess) {
+    cleanup();
+    return c->cuda_error(e, "grt_pade alloc");
+  }
+  cudaStream_t s = c->stream;
+  if ((e = cudaMemcpyAsync(dc.ptr, coef, (size_t)n * (K + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = grt::launch_pade((int)n, K, L, M, dc.as<double>(), du.as<double>(), ds.as<int32_t>(), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(u_out, du.ptr, (size_t)n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (status_out && (e = cudaMemcpyAsync(status_out, ds.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cleanup();
+    return c->cuda_error(e, "grt_pade");
+  }
+  cleanup();
+  return GRT_OK;
+}
+
+int grt_trees(grt_ctx *c, const double *x, double t, uint64_t point_index, uint64_t first_tree, uint64_t ntrees, int K,
+              uint64_t seed, int32_t *order, double *w, uint32_t *nodes, uint64_t *hash) {
+  if (!c) return GRT_EINVAL;
+  if (!x) return c->set_error(GRT_EINVAL, "x is NULL");
+  if (K < 0 || K > GRT_MAX_K) return c->set_error(GRT_EINVAL, "K must be in [0, 16]");
+  if (!(is_finite(t) && t >= 0.0)) return c->set_error(GRT_EINVAL, "t must be finite and >= 0");
+  for (int d = 0; d < c->pb.dim; ++d)
+    if (!is_finite(x[d])) return c->set_error(GRT_EINVAL, "x must be finite");
+  if (point_index > 0xFFFFFFFFull || first_tree + ntrees > 0x80000000ull)
+    return c->set_error(GRT_EINVAL, "point_index must be < 2^32 and first_tree + ntrees <= 2^31");
+  if (ntrees == 0) return GRT_OK;
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  grt::WalkParams p = c->base;
+  set_round_keys(p, seed);
+  p.K = K;
+  double x0[3] = {0, 0, 0};
+  for (int d = 0; d < c->pb.dim; ++d) x0[d] = x[d];
+  DevBuf bo, bw, bn, bh;
+  auto cleanup = [&]() {
+    bo.release();
+    bw.release();
+    bn.release();
+    bh.release();
+  };
+  cudaError_t e;
+  if ((e = bo.ensure(ntrees * 4)) != cudaSuccess || (e = bw.ensure(ntrees * 8)) != cudaSuccess ||
+      (e = bn.ensure(ntrees * 4)) != cudaSuccess || (e = bh.ensure(ntrees * 8)) != cudaSuccess) {
+    cleanup();
+    return c->cuda_error(e, "grt_trees alloc");
+  }
+  cudaStream_t s = c->stream;
+  if ((e = grt::launch_trees(c->pb.precision == GRT_FP64, c->pb.dim, c->pb.strategy, p, x0, t, (uint32_t)point_index,
+                             (uint32_t)first_tree, (uint32_t)ntrees, bo.as<int32_t>(), bw.as<double>(),
+                             bn.as<uint32_t>(), bh.as<uint64_t>(), s)) != cudaSuccess ||
+      (order && (e = cudaMemcpyAsync(order, bo.ptr, ntrees * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (w && (e = cudaMemcpyAsync(w, bw.ptr, ntrees * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (nodes && (e = cudaMemcpyAsync(nodes, bn.ptr, ntrees * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (hash && (e = cudaMemcpyAsync(hash, bh.ptr, ntrees * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cleanup();
+    return c->cuda_error(e, "grt_trees");
+  }
+  cleanup();
+  return GRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+// grt_device.cuh -- device-side building blocks of the random-tree walk.
+//
+// One node of a generalized random tree (Sec. 2.1 algorithm / Fig. 1 for
+// Strategy A, Sec. 2.2 Eqs. probexpB1-probexpBclosed for Strategy B):
+//   draw the node's Philox words, sample its Brownian segment exactly
+//   (variance 2 D s per axis: Eqs. green, SDE with sigma^2 = 2D), decide
+//   leaf / split, and return the factor it multiplies into the tree weight.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grt {
+
+constexpr int kMaxTerms = 16;     // powers 0..15 of f
+constexpr int kMaxK = 16;         // highest series order
+constexpr int kTile = 512;        // trees per work item (fixed: it defines the summation order)
+constexpr int kWarpsPerBlock = 4; // persistent walk kernel
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4 };
+enum : int { kStratA = 0, kStratB = 1 };
+
+// Everything one walk launch needs, passed by value (constant bank).
+struct WalkParams {
+  // branching law
+  int ncat_thr;              // number of finite thresholds used by the first categorical draw
+  uint32_t thr[kMaxTerms + 1];
+  int nterms;
+  int arity[kMaxTerms];
+  double term_factor[kMaxTerms];  // B: b_k / P(k);  A: b_k / (lambda P(k))
+  double leaf_factor;             // B: 1 / P(leaf)
+  // problem scalars
+  int u0_kind;
+  int K;
+  double two_D;
+  double inv_lambda;   // A
+  double lam_minus_c;  // A
+  double u0d[8];       // u0 constants (see make_u0_constants on the host)
+  float u0f[8];
+  float two_Df, inv_lambdaf, lam_minus_cf;
+  // Philox round keys: round r uses (k0 + r W0, k1 + r W1)
+  uint32_t rk0[10], rk1[10];
+  uint32_t point_base;
+  // data
+  const double *x;           // [n][dim]
+  const double *t;           // [n]
+  const uint32_t *ntrees;    // [n]
+  const uint32_t *prefix;    // [n+1] first work item of each point
+  int n;
+  uint32_t total_items;
+  void *part;                // [items][3][K+1] sums (float or double)
+  uint32_t *cnt;             // [items][K+3] counts 0..K, pruned, nodes
+  uint32_t *counter;         // work-queue head
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each round multiplies
+// words 0 and 2 by the two round constants (32x32 -> 64 bit), and the key of
+// round r is the launch key advanced r times by the Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
+// U(w) = ((w >> 9) + 1/2) 2^-23 in (0,1).  In binary32 it is formed exactly:
+// the float 1 + (w>>9) 2^-23 minus (1 - 2^-24) is exact by Sterbenz' lemma.
+template <typename Real> __device__ __forceinline__ Real uniform01(uint32_t w);
+template <> __device__ __forceinline__ float uniform01<float>(uint32_t w) {
+  return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), __uint_as_float(0x3F7FFFFFu));
+}
+template <> __device__ __forceinline__ double uniform01<double>(uint32_t w) {
+  return __dadd_rn((double)(w >> 9), 0.5) * 0x1p-23;
+}
+
+template <typename Real> struct Math;
+template <> struct Math<float> {
+  static __device__ __forceinline__ float log(float v) { return logf(v); }
+  static __device__ __forceinline__ float sqrt(float v) { return sqrtf(v); }
+  static __device__ __forceinline__ float exp(float v) { return expf(v); }
+  static __device__ __forceinline__ float cos(float v) { return cosf(v); }
+  static __device__ __forceinline__ float tanh(float v) { return tanhf(v); }
+  static __device__ __forceinline__ float abs(float v) { return fabsf(v); }
+  static __device__ __forceinline__ void sincospi(float v, float *s, float *c) { sincospif(v, s, c); }
+  static __device__ __forceinline__ float cospi(float v) { return cospif(v); }
+};
+template <> struct Math<double> {
+  static __device__ __forceinline__ double log(double v) { return ::log(v); }
+  static __device__ __forceinline__ double sqrt(double v) { return ::sqrt(v); }
+  static __device__ __forceinline__ double exp(double v) { return ::exp(v); }
+  static __device__ __forceinline__ double cos(double v) { return ::cos(v); }
+  static __device__ __forceinline__ double tanh(double v) { return ::tanh(v); }
+  static __device__ __forceinline__ double abs(double v) { return fabs(v); }
+  static __device__ __forceinline__ void sincospi(double v, double *s, double *c) { ::sincospi(v, s, c); }
+  static __device__ __forceinline__ double cospi(double v) { return ::cospi(v); }
+};
+
+template <typename Real> __device__ __forceinline__ Real pconst(const WalkParams &p, int i);
+template <> __device__ __forceinline__ float pconst<float>(const WalkParams &p, int i) { return p.u0f[i]; }
+template <> __device__ __forceinline__ double pconst<double>(const WalkParams &p, int i) { return p.u0d[i]; }
+
+// Initial data g at y.  Constants (host-prepared):
+//   GAUSS     c0, A, -1/(2 s^2), x0, y0, z0
+//   COS_PROD  c0, A, w0, w1, w2
+//   TANH_PROD c0, A, s0, s1, s2
+//   LOGISTIC  c0, A, x0, -1/width
+template <typename Real, int DIM>
+__device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&y)[DIM]) {
+  using M = Math<Real>;
+  const Real c0 = pconst<Real>(p, 0), A = pconst<Real>(p, 1);
+  switch (p.u0_kind) {
+  case kU0Gauss: {
+    Real r2 = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const Real e = y[i] - pconst<Real>(p, 3 + i);
+      r2 += e * e;
+    }
+    return c0 + A * M::exp(r2 * pconst<Real>(p, 2));
+  }
+  case kU0CosProd: {
+    Real pr = Real(1);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) pr *= M::cos(pconst<Real>(p, 2 + i) * y[i]);
+    return c0 + A * pr;
+  }
+  case kU0TanhProd: {
+    Real pr = Real(1);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) pr *= M::tanh(y[i] - pconst<Real>(p, 2 + i));
+    return c0 + A * pr;
+  }
+  case kU0Logistic:
+    return c0 + A / (Real(1) + M::exp((y[0] - pconst<Real>(p, 2)) * pconst<Real>(p, 3)));
+  default:
+    return c0;
+  }
+}
+
+template <typename Real> struct Scalars;
+template <> struct Scalars<float> {
+  static __device__ __forceinline__ float two_D(const WalkParams &p) { return p.two_Df; }
+  static __device__ __forceinline__ float inv_lambda(const WalkParams &p) { return p.inv_lambdaf; }
+  static __device__ __forceinline__ float lam_minus_c(const WalkParams &p) { return p.lam_minus_cf; }
+};
+template <> struct Scalars<double> {
+  static __device__ __forceinline__ double two_D(const WalkParams &p) { return p.two_D; }
+  static __device__ __forceinline__ double inv_lambda(const WalkParams &p) { return p.inv_lambda; }
+  static __device__ __forceinline__ double lam_minus_c(const WalkParams &p) { return p.lam_minus_c; }
+};
+
+// Index of the first category whose threshold exceeds w, counted over the
+// finite thresholds thr[first .. first+count-1] (the last category's
+// threshold is 2^32 and never stored).
+__device__ __forceinline__ int categorical(const WalkParams &p, uint32_t w, int first, int count) {
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < kMaxTerms; ++j)
+    if (j < count) c += (w >= p.thr[first + j]) ? 1 : 0;
+  return c;
+}
+
+// Result of one node.
+template <typename Real, int DIM> struct NodeOut {
+  Real y[DIM];   // end of the node's Brownian segment
+  Real tau_c;    // remaining time of its children
+  Real factor;   // multiplies the tree weight (includes g(y) at a leaf)
+  int cat;       // term index (split) or -1 (leaf)
+};
+
+// One node: the draws, the segment, the decision and the factor.
+//   Strategy B: leaf with probability q, weight g(x + sqrt(2 D tau) n) / q; else
+//     term k with probability (1-q) p_k, split at tau S (S ~ U(0,1)), weight
+//     tau b_k / ((1-q) p_k), children at remaining time tau (1 - S).
+//   Strategy A: lifetime S = -ln(U)/lambda; S >= tau: leaf with weight
+//     e^{(lambda-c) tau} g(x + sqrt(2 D tau) n); else split at S with weight
+//     e^{(lambda-c) S} b_k / (lambda p_k), children at remaining time tau - S.
+// `s_factor` / the caller's arity table are block-shared copies of the tables.
+template <typename Real, int DIM, int STRAT>
+__device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor, const Real (&x)[DIM],
+                                          Real tau, uint64_t id, uint32_t tree, uint32_t point,
+                                          NodeOut<Real, DIM> &o) {
+  using M = Math<Real>;
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree, point), p.rk0, p.rk1);
+  // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
+  Real n[DIM];
+  {
+    const Real r = M::sqrt(Real(-2) * M::log(uniform01<Real>(w.z)));
+    Real s, c;
+    M::sincospi(Real(2) * uniform01<Real>(w.w), &s, &c);
+    n[0] = r * c;
+    if (DIM > 1) n[DIM > 1 ? 1 : 0] = r * s;
+  }
+  if (DIM == 3) {
+    const uint4 w2 = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree | 0x80000000u, point),
+                                   p.rk0, p.rk1);
+    const Real r = M::sqrt(Real(-2) * M::log(uniform01<Real>(w2.x)));
+    n[DIM - 1] = r * M::cospi(Real(2) * uniform01<Real>(w2.y));
+  }
+
+  bool leaf;
+  Real seg, S;
+  if (STRAT == kStratB) {
+    const int c = categorical(p, w.x, 0, p.ncat_thr);
+    leaf = (c == 0);
+    o.cat = c - 1;
+    S = uniform01<Real>(w.y);
+    seg = leaf ? tau : tau * S;
+    o.tau_c = tau * (Real(1) - S);
+  } else {
+    S = -M::log(uniform01<Real>(w.x)) * Scalars<Real>::inv_lambda(p);
+    leaf = (S >= tau) || (p.nterms == 0);
+    seg = leaf ? tau : S;
+    o.tau_c = tau - S;
+    o.cat = leaf ? -1 : categorical(p, w.y, 0, p.ncat_thr);
+  }
+  const Real sc = M::sqrt(Scalars<Real>::two_D(p) * seg);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
+
+  if (leaf) {
+    const Real g = initial_data<Real, DIM>(p, o.y);
+    if (STRAT == kStratB) {
+      o.factor = (Real)p.leaf_factor * g;
+    } else {
+      const Real lmc = Scalars<Real>::lam_minus_c(p);
+      o.factor = (lmc == Real(0)) ? g : M::exp(lmc * tau) * g;
+    }
+  } else {
+    const Real tf = s_factor[o.cat];
+    if (STRAT == kStratB) {
+      o.factor = tau * tf;
+    } else {
+      const Real lmc = Scalars<Real>::lam_minus_c(p);
+      o.factor = (lmc == Real(0)) ? tf : M::exp(lmc * S) * tf;
+    }
+  }
+}
+
+}  // namespace grt

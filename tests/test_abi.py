@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every call include/grt.h declares, and validates on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2402_06491_gb300 import _binding
+
+    return _binding._load()
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "grt.h")).read()
+    return sorted(set(re.findall(r"\b(grt_[a-z_]+)\s*\(", hdr)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "grt_solve" in names and "grt_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    import paper_2402_06491_gb300 as pkg
+
+    for name in names:
+        assert name in pkg.EXPORTED and callable(getattr(pkg, name)), name
+
+
+def test_library_is_the_in_tree_build(lib):
+    import paper_2402_06491_gb300 as pkg
+
+    assert os.path.dirname(pkg.library_path()) == os.path.join(ROOT, "paper_2402_06491_gb300")
+    assert os.path.exists(pkg.library_path())
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("dim", 4, "dim"), ("D", -1.0, "D must"), ("q", 1.0, "0 < q < 1"), ("q", 0.0, "0 < q < 1"),
+    ("strategy", "C", None), ("u0", ("gauss", (0.0, 1.0, 0.0)), "width"),
+])
+def test_invalid_problems_are_rejected_before_any_device_call(lib, field, value, needle):
+    import paper_2402_06491_gb300 as pkg
+
+    pb = workloads.problem_sin_2d()
+    pb[field] = value
+    if field == "strategy":
+        with pytest.raises(KeyError):
+            pkg.problem_struct(pb)
+        return
+    with pytest.raises(pkg.GrtError) as ei:
+        pkg.grt_create(pb)
+    assert ei.value.code == -1
+    assert needle in str(ei.value)
+
+
+def test_strategy_a_needs_positive_rate(lib):
+    import paper_2402_06491_gb300 as pkg
+
+    pb = workloads.problem_kpp_1d()
+    pb["lam"] = 0.0
+    with pytest.raises(pkg.GrtError) as ei:
+        pkg.grt_create(pb)
+    assert ei.value.code == -1 and "lambda" in str(ei.value)
+
+
+def test_null_arguments(lib):
+    out = ctypes.c_void_p()
+    assert lib.grt_create(None, 0, ctypes.byref(out)) == -1
+    assert out.value is None
+    lib.grt_destroy(None)
+    lib.grt_plan_destroy(None)
+    assert lib.grt_solve(None, 0, None, None, None, 0, 0, 0, 0, 0, None, None, None, None) == -1
+    assert lib.grt_plan_launches(None) == 0

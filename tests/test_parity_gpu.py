@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path against the FP64 oracle on the same random streams.
+
+Bars (spec tolerance; the reading of it near u = 0 is documented):
+  * integer results (tree order Ne, node counts, topology hashes, pruned counts)
+    bit-exact for Strategy B at any precision and for FP64 walks;
+  * FP64 walks: coefficients and Pade values to 1e-12 relative;
+  * FP32 walks: coefficient a_n within 1e-5 of the mean |tree weight| of its
+    order, and the Pade value within 1e-5 * max(|u|, sum_n |a_n|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def grt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2402_06491_gb300 as pkg
+
+    return pkg
+
+
+def _solve_both(grt, pb, x, t, nt, K, L, M, seed, point_base=0):
+    ctx = grt.grt_create(pb, 0)
+    g = grt.grt_solve(ctx, x, t, nt, K, L, M, seed, point_base)
+    ctx.close()
+    o = oracle.solve(pb, x, t, nt, K, L, M, seed, point_base)
+    return g, o
+
+
+def _assert_fp32_parity(g, o, nt, rtol=1e-5):
+    N = np.maximum(np.asarray(nt, float), 1.0)[:, None]
+    scale_coef = o["sa"] / N  # mean |W| of each order: the natural scale of a_n
+    err = np.abs(g["coef"] - o["coef"])
+    assert np.all(err <= rtol * scale_coef + 1e-300), np.max(err / np.maximum(scale_coef, 1e-300))
+    scale_u = np.maximum(np.abs(o["u"]), np.abs(o["coef"]).sum(axis=1))
+    du = np.abs(g["u"] - o["u"])
+    bad = np.where(~(du <= rtol * scale_u))[0]
+    assert bad.size == 0, [(int(i), g["u"][i], o["u"][i], scale_u[i]) for i in bad[:10]]
+    assert np.array_equal(g["status"], o["status"])
+
+
+# ---------------------------------------------------------------------------
+# per-tree parity
+# ---------------------------------------------------------------------------
+PER_TREE = [
+    ("sin_2d B fp32", workloads.problem_sin_2d(), [0.7, -1.2], 1.0, 10),
+    ("pdd_3d B fp32", workloads.problem_pdd_3d(), [2.0, 1.5, 2.5], 1.0, 12),
+    ("uneven_2d B fp32", workloads.problem_uneven_2d(), [3.0, 4.5], 1.7, 16),
+    ("kpp_1d A fp64", workloads.problem_kpp_1d(), [0.3], 0.5, 8),
+    ("wave 1d B fp64", dict(dim=1, D=1.0, f_coef=[0.0, -0.25, 1.25, -1.0], u0=("logistic", (0.0, 1.0, 0.0, 1.4142)),
+                            strategy="B", q=0.7, arity_law="uniform", precision="fp64"), [0.4], 0.8, 10),
+    ("const-term B fp32", dict(dim=2, D=0.3, f_coef=[0.5, 0.0, 1.0], u0=("cos_prod", (0.2, 1.0, 0.5, 1.5)),
+                               strategy="B", q=0.55, arity_law="abs", precision="fp32"), [0.1, 0.2], 0.9, 10),
+]
+
+
+@pytest.mark.parametrize("name,pb,x,t,K", PER_TREE, ids=[c[0] for c in PER_TREE])
+def test_per_tree_records(grt, name, pb, x, t, K):
+    ntrees = 20_000
+    ctx = grt.grt_create(pb, 0)
+    g = grt.grt_trees(ctx, x, t, 77, 1000, ntrees, K, 5)
+    ctx.close()
+    o = oracle.trees(pb, x, t, 77, 1000, ntrees, K, 5)
+    assert np.array_equal(g["order"], o["order"])
+    assert np.array_equal(g["nodes"], o["nodes"])
+    assert np.array_equal(g["hash"], o["hash"])
+    rtol = 1e-12 if pb["precision"] == "fp64" else 3e-5
+    assert np.all(np.abs(g["w"] - o["w"]) <= rtol * np.abs(o["w"]) + 1e-300), np.max(
+        np.abs(g["w"] - o["w"]) / np.maximum(np.abs(o["w"]), 1e-300))
+
+
+def test_strategy_a_fp32_topology_mismatches_are_rare(grt):
+    # FP32 lifetimes S = -ln(U)/lambda compared with FP32 remaining times can flip a
+    # leaf/split decision when S and tau agree to ~1e-7: count them (bound 1e-3 of trees).
+    pb = dict(dim=2, D=0.5, f_coef=[0.0, -0.3, 1.0, -0.5], u0=("gauss", (0.2, 1.0, 0.8, 0.0, 0.0)), strategy="A",
+              lam=1.2, c_pot=0.3, arity_law="uniform", precision="fp32")
+    ntrees = 20_000
+    ctx = grt.grt_create(pb, 0)
+    g = grt.grt_trees(ctx, [0.3, -0.4], 0.9, 3, 0, ntrees, 10, 9)
+    ctx.close()
+    o = oracle.trees(pb, [0.3, -0.4], 0.9, 3, 0, ntrees, 10, 9)
+    same = g["hash"] == o["hash"]
+    assert (~same).sum() <= max(2, ntrees // 1000)
+    assert np.all(np.abs(g["w"][same] - o["w"][same]) <= 3e-5 * np.abs(o["w"][same]) + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# point solves: several 512-tree tiles plus a ragged tail
+# ---------------------------------------------------------------------------
+def test_kpp_1d_full_workload_fp64(grt):
+    wl = workloads.workload_kpp_1d()
+    g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
+    assert np.allclose(g["coef"], o["coef"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(g["se"], o["se"], rtol=1e-9, atol=1e-15)
+    assert np.allclose(g["u"], o["u"], rtol=1e-12, atol=1e-15)
+    assert np.array_equal(g["status"], o["status"])
+
+
+@pytest.mark.parametrize("name,ntrees", [("sin_2d", 2600), ("pdd_3d", 1500), ("uneven_2d", 3000)])
+def test_point_solve_fp32(grt, name, ntrees):
+    wl = workloads.subsample(workloads.WORKLOADS[name](), 24, ntrees=ntrees)
+    g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
+    _assert_fp32_parity(g, o, wl["ntrees"])
+
+
+def test_edge_budgets_and_orders(grt):
+    pb = workloads.problem_sin_2d()
+    nt = np.array([0, 1, 2, 31, 32, 33, 511, 512, 513, 1024, 1537], np.uint64)
+    x = np.linspace(-1.0, 1.0, 2 * nt.size).reshape(-1, 2)
+    t = np.linspace(0.1, 1.0, nt.size)
+    for K, L, M in [(10, 5, 5), (0, 0, 0), (3, 1, 2), (16, 0, 16)]:
+        g, o = _solve_both(grt, pb, x, t, nt, K, L, M, 123)
+        _assert_fp32_parity(g, o, nt)
+        assert g["u"][0] == 0.0 and np.all(g["coef"][0] == 0.0)
+
+
+def test_empty_call(grt):
+    ctx = grt.grt_create(workloads.problem_sin_2d(), 0)
+    r = grt.grt_solve(ctx, np.zeros((0, 2)), np.zeros(0), np.zeros(0, np.uint64), 10, 5, 5, 0)
+    assert r["u"].shape == (0,)
+    with pytest.raises(grt.GrtError):
+        grt.grt_solve(ctx, np.zeros((1, 2)), [-1.0], [10], 10, 5, 5, 0)
+    with pytest.raises(grt.GrtError):
+        grt.grt_solve(ctx, np.zeros((1, 2)), [1.0], [10], 10, 6, 5, 0)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# determinism: a point's result depends only on its own inputs and global index
+# ---------------------------------------------------------------------------
+def test_alone_and_in_the_mix_are_bit_identical(grt):
+    wl = workloads.subsample(workloads.workload_uneven_2d(), 40, ntrees=4000)
+    ctx = grt.grt_create(wl["problem"], 0)
+    args = (wl["K"], wl["L"], wl["M"], wl["seed"])
+    mix = grt.grt_solve(ctx, wl["x"], wl["t"], wl["ntrees"], *args)
+    again = grt.grt_solve(ctx, wl["x"], wl["t"], wl["ntrees"], *args)
+    assert np.array_equal(mix["u"], again["u"]) and np.array_equal(mix["coef"], again["coef"])
+    for i in (0, 7, 39):
+        alone = grt.grt_solve(ctx, wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], *args, point_base=i)
+        assert np.array_equal(alone["coef"][0], mix["coef"][i])
+        assert alone["u"][0] == mix["u"][i] or (np.isnan(alone["u"][0]) and np.isnan(mix["u"][i]))
+    ctx.close()
+
+
+def test_device_resident_plan_matches_host_solve(grt):
+    torch = pytest.importorskip("torch")
+    wl = workloads.subsample(workloads.workload_sin_2d(), 32, ntrees=5000)
+    n, K = wl["x"].shape[0], wl["K"]
+    ctx = grt.grt_create(wl["problem"], 0)
+    host = grt.grt_solve(ctx, wl["x"], wl["t"], wl["ntrees"], K, wl["L"], wl["M"], wl["seed"])
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, wl["L"], wl["M"])
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(wl["x"]).to(dev)
+    t = torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, st, stream=s)
+    s.synchronize()
+    assert np.array_equal(u.cpu().numpy(), host["u"])
+    assert np.array_equal(coef.cpu().numpy(), host["coef"])
+    nodes, splits, pruned = grt.grt_plan_counters(plan)
+    o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], K, wl["L"], wl["M"], wl["seed"])
+    assert nodes == int(o["nodes"].sum())
+    assert pruned == int(o["cnt"][:, K + 1].sum())
+    cnt = o["cnt"].astype(np.int64)
+    assert splits == int((cnt[:, : K + 2] * np.arange(K + 2)).sum())
+    assert grt.grt_plan_launches(plan) == 2
+    plan.close()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# the Pade stage alone
+# ---------------------------------------------------------------------------
+def test_pade_stage_alone(grt):
+    ctx = grt.grt_create(workloads.problem_sin_2d(), 0)
+    rng = np.random.default_rng(3)
+    cases = []
+    for L, M in [(4, 4), (5, 5), (8, 8), (3, 2), (2, 5), (0, 3), (6, 0)]:
+        C = rng.normal(size=(50, 17))
+        C[:, L + M + 1:] = 0.0
+        cases.append((L, M, C))
+    geo = np.array([[0.8 ** (n + 1) * tt ** n for n in range(17)] for tt in (0.5, 1.0, 2.0, 5.0)])
+    cases.append((4, 4, geo))
+    cases.append((4, 4, np.zeros((2, 17))))
+    cases.append((4, 4, np.ones((2, 17))))
+    for L, M, C in cases:
+        u, st = grt.grt_pade(ctx, C, L, M)
+        for i in range(C.shape[0]):
+            uo, so, _ = oracle.pade(C[i], L, M)
+            assert st[i] == so, (L, M, i)
+            if np.isfinite(uo) and abs(uo) < 1e12:
+                assert abs(u[i] - uo) <= 1e-10 * max(1.0, abs(uo)), (L, M, i, u[i], uo)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# the benchmarked workload at full size, sampled points
+# ---------------------------------------------------------------------------
+def test_full_size_sin_2d_sampled_points(grt):
+    """sin_2d at its full size (512 point solves x 1e5 trees) in the launch configuration the
+    benchmark times; 6 sampled points recomputed one by one by the oracle (same global index)."""
+    wl = workloads.workload_sin_2d()
+    ctx = grt.grt_create(wl["problem"], 0)
+    g = grt.grt_solve(ctx, wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
+    ctx.close()
+    assert np.all(np.isfinite(g["u"]))
+    for i in (0, 77, 255, 256, 300, 511):
+        o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], wl["K"], wl["L"],
+                         wl["M"], wl["seed"], point_base=i)
+        gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
+        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1])
