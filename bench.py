@@ -94,7 +94,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, bus_id: str | None):
-        self.bus_id = (bus_id or "").lower()
+        self.bus_id = (bus_id or "").lower()  # e.g. "00000009:01:00.0"; empty = only GPU of the box
         self.samples = []
         self.proc = None
         self.thread = None
@@ -115,7 +115,7 @@ class ClockSampler:
             if len(parts) < 10:
                 continue
             bus = parts[1].lower()
-            if self.bus_id and not (bus.endswith(self.bus_id[-12:]) or self.bus_id.endswith(bus[-12:])):
+            if self.bus_id and bus[-7:] != self.bus_id[-7:]:
                 continue
             try:
                 self.samples.append(dict(t=time.time(), sm=float(parts[2]), sm_max=float(parts[3]),
@@ -179,6 +179,25 @@ def run_oracle(wl: dict, npts: int, nthreads: int):
     return time.perf_counter() - t0, r
 
 
+def cpu_baseline(wl: dict, target_s: float) -> dict:
+    """The oracle, as it stands, on all host cores over the leading points of the workload.
+
+    Whole passes over the chosen points are repeated until about target_s of wall time.
+    """
+    nthreads = os.cpu_count() or 1
+    npts = oracle_sample(wl, target_s, nthreads)
+    trees = float(np.sum(wl["ntrees"][:npts]))
+    total, reps = 0.0, 0
+    while reps == 0 or (total < 0.5 * target_s and reps < 20):
+        dt, _ = run_oracle(wl, npts, nthreads)
+        total += dt
+        reps += 1
+    n = wl["x"].shape[0]
+    return {"value": trees * reps / total, "unit": "trees/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each) x {reps} pass(es), "
+                      f"{total:.1f} s wall on {nthreads} threads"}
+
+
 def reference_arm(args) -> int:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -240,6 +259,8 @@ def gpu_arm(args) -> int:
     import paper_2402_06491_gb300 as grt
 
     wl = workloads.WORKLOADS[WORKLOAD]()
+    if args.trees:
+        wl["ntrees"] = np.full_like(wl["ntrees"], args.trees)
     n, K, L, M = wl["x"].shape[0], wl["K"], wl["L"], wl["M"]
     point_base = rank * n
     trees_per_step = float(np.sum(wl["ntrees"]))
@@ -265,8 +286,11 @@ def gpu_arm(args) -> int:
     nodes, splits, pruned = grt.grt_plan_counters(plan)
 
     props = torch.cuda.get_device_properties(dev)
-    bus = getattr(props, "pci_bus_id", None)
-    sampler = ClockSampler(f"{bus:02x}" if isinstance(bus, int) else None)
+    bus, devid = getattr(props, "pci_bus_id", None), getattr(props, "pci_device_id", None)
+    bus_str = f"{bus:02x}:{devid:02x}.0" if isinstance(bus, int) and isinstance(devid, int) else None
+    if torch.cuda.device_count() == 1 and not os.environ.get("CUDA_VISIBLE_DEVICES"):
+        bus_str = None
+    sampler = ClockSampler(bus_str)
     sampler.start()
     time.sleep(0.3)
 
@@ -306,26 +330,26 @@ def gpu_arm(args) -> int:
     finite = bool(np.all(np.isfinite(u_host)))
 
     # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result
+    e2e_steps = 0 if args.no_e2e else max(args.steps, 1)
     xh = torch.from_numpy(wl["x"]).pin_memory().numpy()
     th = torch.from_numpy(wl["t"]).pin_memory().numpy()
     nth = torch.from_numpy(wl["ntrees"].astype(np.int64)).pin_memory().numpy().view(np.uint64)
     uh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     sth = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
     out = {"u": uh, "status": sth}
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(args.warmup, 1) if e2e_steps else 0):
         grt.grt_solve(ctx, xh, th, nth, K, L, M, wl["seed"], point_base, want_coef=False, want_se=False, out=out)
-    e2e_steps = max(args.steps, 1)
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         grt.grt_solve(ctx, xh, th, nth, K, L, M, wl["seed"], point_base, want_coef=False, want_se=False, out=out)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     if dist is not None:
         te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e_s = float(te.item())
-    same = bool(np.array_equal(uh, u_host))
+    same = bool(np.array_equal(uh, u_host)) if e2e_steps else None
     h2d = xh.nbytes + th.nbytes
     d2h = uh.nbytes + sth.nbytes
 
@@ -371,22 +395,15 @@ def gpu_arm(args) -> int:
             "walk_ms": walk_avg_ms, "finalize_ms": float(np.mean(fin_ms)),
             "peak_basis": f"{SM_COUNT_GB300} SMs x 4 issue slots/clk x 32 threads x {sm_max:.0f} MHz (max SM clock)",
         },
-        "e2e": {"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps, "matches_device_run": same},
+        "e2e": ({"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
+                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "matches_device_run": same} if e2e_steps else None),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "finite_output": finite,
     }
     if world == 1 and not args.no_cpu_baseline:
-        nthreads = os.cpu_count() or 1
-        target = float(os.environ.get("GRT_CPU_BASELINE_S", "15"))
-        npts = oracle_sample(wl, target, nthreads)
-        dt, _ = run_oracle(wl, npts, nthreads)
-        line["cpu_baseline"] = {"value": float(np.sum(wl["ntrees"][:npts])) / dt, "unit": "trees/s", "cores": nthreads,
-                                "kind": "oracle",
-                                "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each), "
-                                          f"{dt:.1f} s wall on {nthreads} threads"}
+        line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")))
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -400,6 +417,8 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="grt", choices=["grt", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--trees", type=int, default=0, help="trees per point (profiling cases; default: the workload's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -106,13 +106,36 @@ template <typename Real> __device__ __forceinline__ Real pconst(const WalkParams
 template <> __device__ __forceinline__ float pconst<float>(const WalkParams &p, int i) { return p.u0f[i]; }
 template <> __device__ __forceinline__ double pconst<double>(const WalkParams &p, int i) { return p.u0d[i]; }
 
-// Initial data g at y.  Constants (host-prepared):
+// Per-point shifted origin of the initial data, formed once per point in FP64.
+// The walk carries each particle's displacement D from its tree's root x_p, and
+// g is evaluated at x_p + D through these offsets, so an FP32 walk keeps full
+// relative accuracy near the initial data's centre, zeros and phases:
+//   GAUSS, TANH_PROD  base_i = x_p,i - centre_i
+//   LOGISTIC          base_0 = x_p,0 - centre
+//   COS_PROD          base_i = omega_i x_p,i reduced to [-pi, pi]
+template <typename Real, int DIM>
+__device__ __forceinline__ void initial_data_base(const WalkParams &p, const double *xp, Real (&base)[DIM]) {
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    double b = 0.0;
+    switch (p.u0_kind) {
+    case kU0Gauss: b = xp[i] - p.u0d[3 + i]; break;
+    case kU0TanhProd: b = xp[i] - p.u0d[2 + i]; break;
+    case kU0Logistic: b = i == 0 ? xp[0] - p.u0d[2] : 0.0; break;
+    case kU0CosProd: b = remainder(p.u0d[2 + i] * xp[i], 6.283185307179586476925286766559); break;
+    default: break;
+    }
+    base[i] = (Real)b;
+  }
+}
+
+// Initial data g at x_p + D.  Constants (host-prepared):
 //   GAUSS     c0, A, -1/(2 s^2), x0, y0, z0
 //   COS_PROD  c0, A, w0, w1, w2
 //   TANH_PROD c0, A, s0, s1, s2
 //   LOGISTIC  c0, A, x0, -1/width
 template <typename Real, int DIM>
-__device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&y)[DIM]) {
+__device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&base)[DIM], const Real (&D)[DIM]) {
   using M = Math<Real>;
   const Real c0 = pconst<Real>(p, 0), A = pconst<Real>(p, 1);
   switch (p.u0_kind) {
@@ -120,7 +143,7 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&y
     Real r2 = Real(0);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      const Real e = y[i] - pconst<Real>(p, 3 + i);
+      const Real e = base[i] + D[i];
       r2 += e * e;
     }
     return c0 + A * M::exp(r2 * pconst<Real>(p, 2));
@@ -128,17 +151,17 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&y
   case kU0CosProd: {
     Real pr = Real(1);
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) pr *= M::cos(pconst<Real>(p, 2 + i) * y[i]);
+    for (int i = 0; i < DIM; ++i) pr *= M::cos(base[i] + pconst<Real>(p, 2 + i) * D[i]);
     return c0 + A * pr;
   }
   case kU0TanhProd: {
     Real pr = Real(1);
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) pr *= M::tanh(y[i] - pconst<Real>(p, 2 + i));
+    for (int i = 0; i < DIM; ++i) pr *= M::tanh(base[i] + D[i]);
     return c0 + A * pr;
   }
   case kU0Logistic:
-    return c0 + A / (Real(1) + M::exp((y[0] - pconst<Real>(p, 2)) * pconst<Real>(p, 3)));
+    return c0 + A / (Real(1) + M::exp((base[0] + D[0]) * pconst<Real>(p, 3)));
   default:
     return c0;
   }
@@ -169,7 +192,7 @@ __device__ __forceinline__ int categorical(const WalkParams &p, uint32_t w, int 
 
 // Result of one node.
 template <typename Real, int DIM> struct NodeOut {
-  Real y[DIM];   // end of the node's Brownian segment
+  Real y[DIM];   // end of the node's Brownian segment (displacement from the root)
   Real tau_c;    // remaining time of its children
   Real factor;   // multiplies the tree weight (includes g(y) at a leaf)
   int cat;       // term index (split) or -1 (leaf)
@@ -182,11 +205,12 @@ template <typename Real, int DIM> struct NodeOut {
 //   Strategy A: lifetime S = -ln(U)/lambda; S >= tau: leaf with weight
 //     e^{(lambda-c) tau} g(x + sqrt(2 D tau) n); else split at S with weight
 //     e^{(lambda-c) S} b_k / (lambda p_k), children at remaining time tau - S.
-// `s_factor` / the caller's arity table are block-shared copies of the tables.
+// `s_factor` / the caller's arity table are block-shared copies of the tables;
+// x is the displacement from the tree's root and `base` the root's shifted origin.
 template <typename Real, int DIM, int STRAT>
-__device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor, const Real (&x)[DIM],
-                                          Real tau, uint64_t id, uint32_t tree, uint32_t point,
-                                          NodeOut<Real, DIM> &o) {
+__device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
+                                          const Real (&base)[DIM], const Real (&x)[DIM], Real tau, uint64_t id,
+                                          uint32_t tree, uint32_t point, NodeOut<Real, DIM> &o) {
   using M = Math<Real>;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree, point), p.rk0, p.rk1);
   // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
@@ -226,7 +250,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
 
   if (leaf) {
-    const Real g = initial_data<Real, DIM>(p, o.y);
+    const Real g = initial_data<Real, DIM>(p, base, o.y);
     if (STRAT == kStratB) {
       o.factor = (Real)p.leaf_factor * g;
     } else {

@@ -93,9 +93,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
     const uint32_t first = (item - __ldg(p.prefix + pt)) * (uint32_t)kTile;
     const uint32_t N = __ldg(p.ntrees + pt);
     const int ntr = (int)min((uint32_t)kTile, N - first);
-    Real x0[DIM];
+    Real base[DIM];
+    {
+      double xp[DIM];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) x0[i] = (Real)__ldg(p.x + (size_t)pt * DIM + i);
+      for (int i = 0; i < DIM; ++i) xp[i] = __ldg(p.x + (size_t)pt * DIM + i);
+      initial_data_base<Real, DIM>(p, xp, base);
+    }
     const Real t0 = (Real)__ldg(p.t + pt);
     const uint32_t point = p.point_base + (uint32_t)pt;
 
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
     uint64_t id = 0;
     int Ne = 0, depth = 0;
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) x[i] = x0[i];
+    for (int i = 0; i < DIM; ++i) x[i] = Real(0);
     int next = 32;
     uint32_t nodes = 0;
 
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
       if (active) {
         ++nodes;
         NodeOut<Real, DIM> o;
-        node_step<Real, DIM, STRAT>(p, s_factor, x, tau, id, first + (uint32_t)tree, point, o);
+        node_step<Real, DIM, STRAT>(p, s_factor, base, x, tau, id, first + (uint32_t)tree, point, o);
         W *= o.factor;
         bool descend = false;
         if (o.cat >= 0) {
@@ -131,9 +135,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
                 stk_tau[at] = o.tau_c;
-                const uint64_t base = id * 16u;
-                stk_lo[at] = (uint32_t)base;
-                stk_hi[at] = (uint32_t)(base >> 32);
+                const uint64_t child0 = id * 16u;  // children of id are child0 + 1 .. child0 + k
+                stk_lo[at] = (uint32_t)child0;
+                stk_hi[at] = (uint32_t)(child0 >> 32);
                 stk_nk[at] = ((uint32_t)k << 8) | 2u;
                 ++depth;
               }
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
           active = tree < ntr;
           if (active) {
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) x[i] = x0[i];
+            for (int i = 0; i < DIM; ++i) x[i] = Real(0);
             tau = t0;
             W = Real(1);
             id = 0;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
 
 // One thread per tree: per-tree records (diagnostic form of the same streams).
 template <typename Real, int DIM, int STRAT>
-__global__ void trees_kernel(const WalkParams p, Real x0_0, Real x0_1, Real x0_2, Real t0, uint32_t point,
+__global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, double x0_2, Real t0, uint32_t point,
                              uint32_t first_tree, uint32_t ntrees, int32_t *order, double *wout, uint32_t *nodes_out,
                              uint64_t *hash_out) {
   __shared__ Real s_factor[kMaxTerms];
@@ -249,10 +253,11 @@ __global__ void trees_kernel(const WalkParams p, Real x0_0, Real x0_1, Real x0_2
   Real sy[kMaxK][DIM], stau[kMaxK];
   uint64_t sbase[kMaxK];
   uint32_t snk[kMaxK];
-  const Real xin[3] = {x0_0, x0_1, x0_2};
-  Real x[DIM];
+  const double xin[3] = {x0_0, x0_1, x0_2};
+  Real base[DIM], x[DIM];
+  initial_data_base<Real, DIM>(p, xin, base);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) x[d] = xin[d];
+  for (int d = 0; d < DIM; ++d) x[d] = Real(0);
   Real tau = t0, W = Real(1);
   uint64_t id = 0, h = 0xCBF29CE484222325ull;
   int Ne = 0, depth = 0;
@@ -262,7 +267,7 @@ __global__ void trees_kernel(const WalkParams p, Real x0_0, Real x0_1, Real x0_2
   for (;;) {
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, x, tau, id, tree, point, o);
+    node_step<Real, DIM, STRAT>(p, s_factor, base, x, tau, id, tree, point, o);
     h = (h ^ (uint64_t)(o.cat + 1)) * 0x100000001B3ull;
     W *= o.factor;
     bool descend = false;
@@ -354,7 +359,7 @@ static cudaError_t launch_trees_t(const WalkParams &p, const double *x0, double 
   const unsigned blocks = (ntrees + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
   trees_kernel<Real, DIM, STRAT><<<blocks, threads, 0, stream>>>(
-      p, (Real)x0[0], (Real)(DIM > 1 ? x0[1] : 0.0), (Real)(DIM > 2 ? x0[2] : 0.0), (Real)t0, point, first, ntrees,
+      p, x0[0], DIM > 1 ? x0[1] : 0.0, DIM > 2 ? x0[2] : 0.0, (Real)t0, point, first, ntrees,
       order, w, nodes, hash);
   return cudaGetLastError();
 }
