@@ -417,16 +417,29 @@ int oracle_trees(const or_problem *pb, const double *x, double t, uint64_t point
 /*   Denominator: beta_0 = 1, sum_{j=1..M} c_{L+i-j} beta_j = -c_{L+i},     */
 /*   i = 1..M (c_{<0} = 0); numerator alpha_i = sum_{j<=min(i,M)} beta_j    */
 /*   c_{i-j}.  Solved on c_n = a_n / rho^n and evaluated at w = rho, which  */
-/*   equals the unscaled approximant at eps = 1.  A pivot below 1e-14 times */
-/*   the largest matrix entry lowers the type to [L-1/M-1] (L stays >= 0).  */
+/*   equals the unscaled approximant at eps = 1 (a Pade approximant is      */
+/*   invariant under eps -> s eps; the paper fixes no scaling).  A pivot    */
+/*   below 1e-14 times the largest matrix entry lowers the type to          */
+/*   [L-1/M-1] (L stays >= 0).                                              */
 /* ------------------------------------------------------------------------ */
 int oracle_pade(int L, int M, const double *a, double *u_out, int32_t *status_out, int32_t *lm_used)
 {
     int32_t status = 0;
     if (L < 0 || M < 0 || L + M > OR_MAX_K) return -1;
     int n = L + M;
-    double rho = 1.0;
-    if (n > 0 && a[0] != 0.0 && a[n] != 0.0) rho = pow(fabs(a[n]) / fabs(a[0]), 1.0 / (double)n);
+    /* Scale: rho = max_{j > m} (|a_j| / |a_m|)^{1/(j-m)}, m the first nonzero
+     * coefficient (the root test's growth rate), so that |c_j| <= |c_m| for all j
+     * and the fastest-growing coefficient matches |c_m|.  rho = 1 when no two
+     * coefficients are nonzero. */
+    double rho = 0.0;
+    int m = 0;
+    while (m <= n && a[m] == 0.0) ++m;
+    for (int j = m + 1; j <= n; ++j)
+        if (a[j] != 0.0) {
+            double r = pow(fabs(a[j]) / fabs(a[m]), 1.0 / (double)(j - m));
+            if (r > rho) rho = r;
+        }
+    if (!(rho > 0.0) || !isfinite(rho)) rho = 1.0;
     double c[OR_MAX_K + 1];
     for (int i = 0; i <= n; ++i) c[i] = a[i] / pow(rho, (double)i);
 

@@ -85,7 +85,7 @@ struct grt_plan {
   uint32_t total_items = 0;
   uint64_t total_trees = 0;
   std::vector<uint64_t> host_ntrees;
-  DevBuf prefix, ntrees, part, cnt, counter, nodes_pt, pruned_pt, splits_pt;
+  DevBuf prefix, tree_prefix, ntrees, rec_w, rec_o, work;  // work: queue head (8 B) + 3 u64 counters
   cudaStream_t last_stream = nullptr;
   int launches = 0;
   bool timing = false, timed_last = false;
@@ -96,14 +96,12 @@ struct grt_plan {
         cudaEventDestroy(e);
         e = nullptr;
       }
-    splits_pt.release();
     prefix.release();
+    tree_prefix.release();
     ntrees.release();
-    part.release();
-    cnt.release();
-    counter.release();
-    nodes_pt.release();
-    pruned_pt.release();
+    rec_w.release();
+    rec_o.release();
+    work.release();
   }
 };
 
@@ -271,29 +269,32 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   p->M = M;
   if (same && p->prefix.ptr) return GRT_OK;
   std::vector<uint32_t> prefix((size_t)n + 1), nt32((size_t)n);
+  std::vector<unsigned long long> tprefix((size_t)n + 1);
   uint64_t items = 0, trees = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
     prefix[(size_t)i] = (uint32_t)items;
+    tprefix[(size_t)i] = trees;
     items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
     trees += ntrees[i];
     nt32[(size_t)i] = (uint32_t)ntrees[i];
     if (items >= 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "too many work items (total trees too large)");
   }
   prefix[(size_t)n] = (uint32_t)items;
+  tprefix[(size_t)n] = trees;
   GRT_CUDA(c, cudaSetDevice(c->device));
   GRT_CUDA(c, p->prefix.ensure(prefix.size() * sizeof(uint32_t)));
+  GRT_CUDA(c, p->tree_prefix.ensure(tprefix.size() * sizeof(unsigned long long)));
   GRT_CUDA(c, p->ntrees.ensure(nt32.size() * sizeof(uint32_t) + 4));
-  GRT_CUDA(c, p->part.ensure((size_t)items * 3 * (K + 1) * acc_size(c) + 16));
-  GRT_CUDA(c, p->cnt.ensure((size_t)items * (K + 3) * sizeof(uint32_t) + 16));
-  GRT_CUDA(c, p->counter.ensure(sizeof(uint32_t)));
-  GRT_CUDA(c, p->nodes_pt.ensure((size_t)n * 8 + 8));
-  GRT_CUDA(c, p->pruned_pt.ensure((size_t)n * 8 + 8));
-  GRT_CUDA(c, p->splits_pt.ensure((size_t)n * 8 + 8));
+  GRT_CUDA(c, p->rec_w.ensure((size_t)trees * acc_size(c) + 16));
+  GRT_CUDA(c, p->rec_o.ensure((size_t)trees + 16));
+  GRT_CUDA(c, p->work.ensure(64));
   GRT_CUDA(c, cudaMemcpy(p->prefix.ptr, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  GRT_CUDA(c, cudaMemcpy(p->tree_prefix.ptr, tprefix.data(), tprefix.size() * sizeof(unsigned long long),
+                         cudaMemcpyHostToDevice));
   if (n > 0)
     GRT_CUDA(c, cudaMemcpy(p->ntrees.ptr, nt32.data(), nt32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  GRT_CUDA(c, cudaMemset(p->counter.ptr, 0, sizeof(uint32_t)));
+  GRT_CUDA(c, cudaMemset(p->work.ptr, 0, 64));
   p->n = n;
   p->total_items = (uint32_t)items;
   p->total_trees = trees;
@@ -317,22 +318,23 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   w.t = d_t;
   w.ntrees = p->ntrees.as<uint32_t>();
   w.prefix = p->prefix.as<uint32_t>();
+  w.tree_prefix = p->tree_prefix.as<unsigned long long>();
   w.n = (int)p->n;
   w.total_items = p->total_items;
-  w.part = p->part.ptr;
-  w.cnt = p->cnt.as<uint32_t>();
-  w.counter = p->counter.as<uint32_t>();
+  w.rec_w = p->rec_w.ptr;
+  w.rec_o = p->rec_o.as<uint8_t>();
+  w.counter = p->work.as<uint32_t>();
+  w.stats = reinterpret_cast<unsigned long long *>(p->work.as<unsigned char>() + 8);
   const bool fp64 = c->pb.precision == GRT_FP64;
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[0], stream));
-  if (p->total_items > 0) {
-    GRT_CUDA(c, cudaMemsetAsync(p->counter.ptr, 0, sizeof(uint32_t), stream));
+  GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, 64, stream));
+  if (p->total_items > 0)
     GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
-  }
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[1], stream));
   grt::FinalizeParams f{};
-  f.part = p->part.ptr;
-  f.cnt = p->cnt.as<uint32_t>();
-  f.prefix = p->prefix.as<uint32_t>();
+  f.rec_w = p->rec_w.ptr;
+  f.rec_o = p->rec_o.as<uint8_t>();
+  f.tree_prefix = p->tree_prefix.as<unsigned long long>();
   f.ntrees = p->ntrees.as<uint32_t>();
   f.n = (int)p->n;
   f.K = p->K;
@@ -342,10 +344,7 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   f.coef = d_coef;
   f.se = d_se;
   f.status = d_status;
-  f.nodes_pt = p->nodes_pt.as<unsigned long long>();
-  f.pruned_pt = p->pruned_pt.as<unsigned long long>();
-  f.splits_pt = p->splits_pt.as<unsigned long long>();
-  f.counter = p->counter.as<uint32_t>();
+  f.stats = w.stats;
   GRT_CUDA(c, grt::launch_finalize(fp64, f, stream));
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[2], stream));
   p->timed_last = p->timing;
@@ -491,23 +490,15 @@ int grt_plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t
 int grt_plan_counters(grt_plan *p, uint64_t *nodes, uint64_t *splits, uint64_t *pruned) {
   if (!p) return GRT_EINVAL;
   grt_ctx *c = p->ctx;
-  uint64_t sn = 0, ss = 0, sp = 0;
+  unsigned long long st[3] = {0, 0, 0};
   if (p->n > 0) {
     GRT_CUDA(c, cudaSetDevice(c->device));
     GRT_CUDA(c, cudaStreamSynchronize(p->last_stream));
-    std::vector<uint64_t> a((size_t)p->n), b((size_t)p->n), d((size_t)p->n);
-    GRT_CUDA(c, cudaMemcpy(a.data(), p->nodes_pt.ptr, a.size() * 8, cudaMemcpyDeviceToHost));
-    GRT_CUDA(c, cudaMemcpy(b.data(), p->pruned_pt.ptr, b.size() * 8, cudaMemcpyDeviceToHost));
-    GRT_CUDA(c, cudaMemcpy(d.data(), p->splits_pt.ptr, d.size() * 8, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < a.size(); ++i) {
-      sn += a[i];
-      sp += b[i];
-      ss += d[i];
-    }
+    GRT_CUDA(c, cudaMemcpy(st, p->work.as<unsigned char>() + 8, sizeof(st), cudaMemcpyDeviceToHost));
   }
-  if (nodes) *nodes = sn;
-  if (splits) *splits = ss;
-  if (pruned) *pruned = sp;
+  if (nodes) *nodes = st[0];
+  if (splits) *splits = st[1];
+  if (pruned) *pruned = st[2];
   return GRT_OK;
 }
 

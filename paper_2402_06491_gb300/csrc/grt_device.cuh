@@ -14,7 +14,8 @@ namespace grt {
 
 constexpr int kMaxTerms = 16;     // powers 0..15 of f
 constexpr int kMaxK = 16;         // highest series order
-constexpr int kTile = 512;        // trees per work item (fixed: it defines the summation order)
+constexpr int kTile = 512;        // trees per work-queue chunk
+constexpr int kFinThreads = 128;  // threads of the finalize kernel (one block per point)
 constexpr int kWarpsPerBlock = 4; // persistent walk kernel
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -46,11 +47,13 @@ struct WalkParams {
   const double *x;           // [n][dim]
   const double *t;           // [n]
   const uint32_t *ntrees;    // [n]
-  const uint32_t *prefix;    // [n+1] first work item of each point
+  const uint32_t *prefix;    // [n+1] first queue chunk of each point
+  const unsigned long long *tree_prefix;  // [n+1] first record of each point
   int n;
-  uint32_t total_items;
-  void *part;                // [items][3][K+1] sums (float or double)
-  uint32_t *cnt;             // [items][K+3] counts 0..K, pruned, nodes
+  uint32_t total_items;      // queue chunks
+  void *rec_w;               // [total trees] tree weights (float or double)
+  uint8_t *rec_o;            // [total trees] tree orders (K+1 = pruned)
+  unsigned long long *stats; // [0] nodes visited (added by the walk)
   uint32_t *counter;         // work-queue head
 };
 
@@ -179,15 +182,14 @@ template <> struct Scalars<double> {
   static __device__ __forceinline__ double lam_minus_c(const WalkParams &p) { return p.lam_minus_c; }
 };
 
-// Index of the first category whose threshold exceeds w, counted over the
-// finite thresholds thr[first .. first+count-1] (the last category's
-// threshold is 2^32 and never stored).
-__device__ __forceinline__ int categorical(const WalkParams &p, uint32_t w, int first, int count) {
-  int c = 0;
-#pragma unroll
-  for (int j = 0; j < kMaxTerms; ++j)
-    if (j < count) c += (w >= p.thr[first + j]) ? 1 : 0;
-  return c;
+// Index of the first category whose threshold exceeds w among the finite
+// thresholds thr[first .. count-1] (the last category's threshold is 2^32 and
+// is not stored): an early-exit scan, since the first categories carry most
+// of the probability.  `thr` is the block-shared copy of the table.
+__device__ __forceinline__ int categorical(const uint32_t *__restrict__ thr, uint32_t w, int first, int count) {
+  int j = first;
+  while (j < count && w >= thr[j]) ++j;
+  return j;
 }
 
 // Result of one node.
@@ -205,12 +207,13 @@ template <typename Real, int DIM> struct NodeOut {
 //   Strategy A: lifetime S = -ln(U)/lambda; S >= tau: leaf with weight
 //     e^{(lambda-c) tau} g(x + sqrt(2 D tau) n); else split at S with weight
 //     e^{(lambda-c) S} b_k / (lambda p_k), children at remaining time tau - S.
-// `s_factor` / the caller's arity table are block-shared copies of the tables;
+// `s_factor`, `s_thr` and the caller's arity table are block-shared copies of the tables;
 // x is the displacement from the tree's root and `base` the root's shifted origin.
 template <typename Real, int DIM, int STRAT>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
-                                          const Real (&base)[DIM], const Real (&x)[DIM], Real tau, uint64_t id,
-                                          uint32_t tree, uint32_t point, NodeOut<Real, DIM> &o) {
+                                          const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
+                                          const Real (&x)[DIM], Real tau, uint64_t id, uint32_t tree, uint32_t point,
+                                          NodeOut<Real, DIM> &o) {
   using M = Math<Real>;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree, point), p.rk0, p.rk1);
   // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
@@ -232,9 +235,9 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   bool leaf;
   Real seg, S;
   if (STRAT == kStratB) {
-    const int c = categorical(p, w.x, 0, p.ncat_thr);
-    leaf = (c == 0);
-    o.cat = c - 1;
+    // joint draw: category 0 is the leaf (w < thr[0]), category j >= 1 is term j - 1
+    leaf = p.ncat_thr == 0 || w.x < s_thr[0];
+    o.cat = leaf ? -1 : categorical(s_thr, w.x, 1, p.ncat_thr) - 1;
     S = uniform01<Real>(w.y);
     seg = leaf ? tau : tau * S;
     o.tau_c = tau * (Real(1) - S);
@@ -243,7 +246,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     leaf = (S >= tau) || (p.nterms == 0);
     seg = leaf ? tau : S;
     o.tau_c = tau - S;
-    o.cat = leaf ? -1 : categorical(p, w.y, 0, p.ncat_thr);
+    o.cat = leaf ? -1 : categorical(s_thr, w.y, 0, p.ncat_thr);
   }
   const Real sc = M::sqrt(Scalars<Real>::two_D(p) * seg);
 #pragma unroll

@@ -22,16 +22,24 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double v) {
 }
 
 // [L/M] Pade of sum a_n eps^n at eps = 1.  The series is first rescaled,
-// c_n = a_n / rho^n with rho = (|a_{L+M}| / |a_0|)^{1/(L+M)}, which leaves the
-// approximant unchanged (evaluated at w = rho) and balances the Toeplitz
-// system  sum_{j=1..M} c_{L+i-j} beta_j = -c_{L+i}, i = 1..M.  Gaussian
+// c_n = a_n / rho^n with rho = max_{j > m} (|a_j| / |a_m|)^{1/(j-m)} (m the
+// first nonzero term), which leaves the approximant unchanged (evaluated at
+// w = rho) and bounds every |c_j| by |c_m| in the Toeplitz system
+// sum_{j=1..M} c_{L+i-j} beta_j = -c_{L+i}, i = 1..M.  Gaussian
 // elimination with partial pivoting; a pivot at or below 1e-14 times the
 // largest entry lowers the type to [L-1/M-1] (L not below 0) and sets
 // PADE_SINGULAR.  |Q(1)| < 1e-8 sets PADE_POLE_NEAR.
 __device__ double pade_value(const double *a, int L, int M, int *status) {
   const int n = L + M;
-  double rho = 1.0;
-  if (n > 0 && a[0] != 0.0 && a[n] != 0.0) rho = pow(fabs(a[n]) / fabs(a[0]), 1.0 / (double)n);
+  // growth rate of the series by the root test, relative to its first nonzero term
+  int first = 0;
+  while (first <= n && a[first] == 0.0) ++first;
+  double rho = 0.0;
+  for (int j = first + 1; j <= n; ++j) {
+    if (a[j] == 0.0) continue;
+    rho = fmax(rho, pow(fabs(a[j]) / fabs(a[first]), 1.0 / (double)(j - first)));
+  }
+  if (!(rho > 0.0) || !isfinite(rho)) rho = 1.0;
   double c[kMaxK + 1];
   for (int i = 0; i <= n; ++i) c[i] = a[i] / pow(rho, (double)i);
 
@@ -107,57 +115,93 @@ __device__ double pade_value(const double *a, int L, int M, int *status) {
   return P / Q;
 }
 
-// One warp per point.  Lane o (o <= K) adds S1, S2, S|W| of order o over the
-// point's items in item order with Kahan compensation; lanes o <= K+2 add the
-// counts (orders, pruned trees, nodes).
+// One block per point.  Thread j bins the point's tree records j, j + T,
+// j + 2T, ... (T = kFinThreads) into its own column of per-order sums in
+// shared memory (S1 with Kahan compensation, S2, S|W|, counts); the columns
+// are then added in a fixed order.  The result depends only on the records.
 template <typename Acc>
-__global__ void __launch_bounds__(32) finalize_kernel(const FinalizeParams f) {
-  const int pt = blockIdx.x;
-  const int lane = threadIdx.x;
-  const int K = f.K;
-  const uint32_t i0 = f.prefix[pt], i1 = f.prefix[pt + 1];
-  const int pstride = 3 * (K + 1), cstride = K + 3;
-  const Acc *part = reinterpret_cast<const Acc *>(f.part);
-  Acc s1 = 0, c1 = 0, s2 = 0, c2 = 0, sa = 0, ca = 0;
-  unsigned long long cn = 0;
-  for (uint32_t it = i0; it < i1; ++it) {
-    if (lane <= K) {
-      const Acc *pp = part + (size_t)it * pstride;
-      kahan_add(s1, c1, pp[lane]);
-      kahan_add(s2, c2, pp[K + 1 + lane]);
-      kahan_add(sa, ca, pp[2 * (K + 1) + lane]);
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeParams f) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int T = kFinThreads;
+  const int pt = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = f.K, R = K + 2;  // rows: orders 0..K and the pruned trees
+  Acc *s1 = reinterpret_cast<Acc *>(smem);  // [R][T] each
+  Acc *c1 = s1 + R * T;
+  Acc *s2 = c1 + R * T;
+  Acc *sa = s2 + R * T;
+  uint32_t *cn = reinterpret_cast<uint32_t *>(sa + R * T);
+  __shared__ double tot[4][kMaxK + 2];
+  for (int r = 0; r < R; ++r) {
+    s1[r * T + tid] = Acc(0);
+    c1[r * T + tid] = Acc(0);
+    s2[r * T + tid] = Acc(0);
+    sa[r * T + tid] = Acc(0);
+    cn[r * T + tid] = 0u;
+  }
+  const unsigned long long r0 = f.tree_prefix[pt], r1 = f.tree_prefix[pt + 1];
+  const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
+  for (unsigned long long i = r0 + tid; i < r1; i += T) {
+    const int o = f.rec_o[i];
+    const Acc w = rw[i];
+    const int a = o * T + tid;
+    if (o <= K) {
+      kahan_add(s1[a], c1[a], w);
+      s2[a] += w * w;
+      sa[a] += w < Acc(0) ? -w : w;
     }
-    if (lane <= K + 2) cn += f.cnt[(size_t)it * cstride + lane];
+    cn[a] += 1u;
   }
-  __shared__ double a[kMaxK + 1];
-  __shared__ unsigned long long pruned;
-  const double N = (double)f.ntrees[pt];
-  if (lane <= K) {
-    const double S1 = (double)s1, S2 = (double)s2;
-    const double an = N > 0.0 ? S1 / N : 0.0;
-    const double var = N > 1.0 ? (S2 / N - an * an) / (N - 1.0) : 0.0;
-    a[lane] = an;
-    if (f.coef) f.coef[(size_t)pt * (K + 1) + lane] = an;
-    if (f.se) f.se[(size_t)pt * (K + 1) + lane] = var > 0.0 ? sqrt(var) : 0.0;
-  }
-  if (lane == K + 1) {
-    pruned = cn;
-    if (f.pruned_pt) f.pruned_pt[pt] = cn;
-  }
-  if (lane == K + 2 && f.nodes_pt) f.nodes_pt[pt] = cn;
-  // splitting events: n per kept tree of order n, K+1 per pruned tree
-  unsigned long long sp = lane <= K + 1 ? (unsigned long long)lane * cn : 0ull;
+  __syncthreads();
+  // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
+  // columns l, l+32, ... with compensation, then a fixed butterfly over lanes
+  for (int r = warp; r < R; r += T / 32) {
+    Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
+    unsigned long long ac = 0;
+    for (int j = lane; j < T; j += 32) {
+      kahan_add(a1, k1, s1[r * T + j] - c1[r * T + j]);
+      kahan_add(a2, k2, s2[r * T + j]);
+      kahan_add(a3, k3, sa[r * T + j]);
+      ac += cn[r * T + j];
+    }
+    double d1 = (double)a1 - (double)k1, d2 = (double)a2 - (double)k2, d3 = (double)a3 - (double)k3;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sp += __shfl_xor_sync(kFull, sp, off);
-  if (lane == 0 && f.splits_pt) f.splits_pt[pt] = sp;
-  __syncwarp();
-  if (lane == 0) {
+    for (int off = 16; off > 0; off >>= 1) {
+      d1 += __shfl_xor_sync(kFull, d1, off);
+      d2 += __shfl_xor_sync(kFull, d2, off);
+      d3 += __shfl_xor_sync(kFull, d3, off);
+      ac += __shfl_xor_sync(kFull, ac, off);
+    }
+    if (lane == 0) {
+      tot[0][r] = d1;
+      tot[1][r] = d2;
+      tot[2][r] = d3;
+      tot[3][r] = (double)ac;
+    }
+  }
+  __syncthreads();
+  __shared__ double a[kMaxK + 1];
+  const double N = (double)f.ntrees[pt];
+  if (tid <= K) {
+    const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
+    const double var = N > 1.0 ? (tot[1][tid] / N - an * an) / (N - 1.0) : 0.0;
+    a[tid] = an;
+    if (f.coef) f.coef[(size_t)pt * (K + 1) + tid] = an;
+    if (f.se) f.se[(size_t)pt * (K + 1) + tid] = var > 0.0 ? sqrt(var) : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double pruned = tot[3][K + 1];
+    double splits = (double)(K + 1) * pruned;
+    for (int o = 1; o <= K; ++o) splits += (double)o * tot[3][o];
     int st = 0;
     const double u = pade_value(a, f.L, f.M, &st);
-    if (N > 0.0 && (double)pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
+    if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
     f.u[pt] = u;
     if (f.status) f.status[pt] = st;
-    if (pt == 0) *f.counter = 0u;  // the walk kernel that used it has finished
+    if (f.stats) {
+      atomicAdd(f.stats + 1, (unsigned long long)splits);
+      atomicAdd(f.stats + 2, (unsigned long long)pruned);
+    }
   }
 }
 
@@ -171,11 +215,17 @@ __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, doub
   if (status) status[i] = st;
 }
 
+template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParams &f, cudaStream_t stream) {
+  const size_t smem = (size_t)(f.K + 2) * kFinThreads * (4 * sizeof(Acc) + sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(finalize_kernel<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  finalize_kernel<Acc><<<f.n, kFinThreads, smem, stream>>>(f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(bool fp64, const FinalizeParams &f, cudaStream_t stream) {
   if (f.n <= 0) return cudaSuccess;
-  if (fp64) finalize_kernel<double><<<f.n, 32, 0, stream>>>(f);
-  else finalize_kernel<float><<<f.n, 32, 0, stream>>>(f);
-  return cudaGetLastError();
+  return fp64 ? launch_finalize_t<double>(f, stream) : launch_finalize_t<float>(f, stream);
 }
 
 cudaError_t launch_pade(int n, int K, int L, int M, const double *coef, double *u, int32_t *status,

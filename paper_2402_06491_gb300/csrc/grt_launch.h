@@ -11,16 +11,15 @@ namespace grt {
 struct WalkParams;
 
 struct FinalizeParams {
-  const void *part;          // [items][3][K+1] item sums (float or double)
-  const uint32_t *cnt;       // [items][K+3]
-  const uint32_t *prefix;    // [n+1]
+  const void *rec_w;         // [total trees] tree weights (float or double)
+  const uint8_t *rec_o;      // [total trees] tree orders (K+1 = pruned)
+  const unsigned long long *tree_prefix;  // [n+1]
   const uint32_t *ntrees;    // [n]
   int n, K, L, M;
   double *u;                 // [n]
   double *coef, *se;         // [n][K+1] or null
   int32_t *status;           // [n] or null
-  unsigned long long *nodes_pt, *pruned_pt, *splits_pt;  // [n] or null
-  uint32_t *counter;         // work-queue head, reset for the next walk
+  unsigned long long *stats; // [1] splitting events, [2] pruned trees (added here)
 };
 
 cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, int num_sms, cudaStream_t stream,
@@ -31,6 +30,5 @@ cudaError_t launch_trees(bool fp64, int dim, int strategy, const WalkParams &p, 
 cudaError_t launch_finalize(bool fp64, const FinalizeParams &f, cudaStream_t stream);
 cudaError_t launch_pade(int n, int K, int L, int M, const double *coef, double *u, int32_t *status,
                         cudaStream_t stream);
-size_t walk_smem_per_block(bool fp64, int dim, int K);
 
 }  // namespace grt
