@@ -85,7 +85,10 @@ struct grt_plan {
   uint32_t total_items = 0;
   uint64_t total_trees = 0;
   std::vector<uint64_t> host_ntrees;
-  DevBuf prefix, tree_prefix, ntrees, rec_w, rec_o, work;  // work: queue head (8 B) + 3 u64 counters
+  uint32_t total_chunks = 0;
+  DevBuf prefix, tree_prefix, ntrees, rec_w, rec_o, chunk_prefix, part;
+  DevBuf work;  // queue head (8 B), 3 u64 counters, then n u32 chunk tickets
+  size_t work_bytes = 64;
   cudaStream_t last_stream = nullptr;
   int launches = 0;
   bool timing = false, timed_last = false;
@@ -101,6 +104,8 @@ struct grt_plan {
     ntrees.release();
     rec_w.release();
     rec_o.release();
+    chunk_prefix.release();
+    part.release();
     work.release();
   }
 };
@@ -264,17 +269,23 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   if (n > 0 && !ntrees) return c->set_error(GRT_EINVAL, "ntrees is NULL");
   const bool same = p->n == n && p->K == K && p->host_ntrees.size() == (size_t)n &&
                     (n == 0 || std::memcmp(p->host_ntrees.data(), ntrees, (size_t)n * sizeof(uint64_t)) == 0);
-  p->K = K;
-  p->L = L;
-  p->M = M;
-  if (same && p->prefix.ptr) return GRT_OK;
+  if (same && p->prefix.ptr) {
+    p->L = L;
+    p->M = M;
+    return GRT_OK;
+  }
+  p->n = -1;  // invalid until the new layout is complete
+  p->host_ntrees.clear();
   std::vector<uint32_t> prefix((size_t)n + 1), nt32((size_t)n);
   std::vector<unsigned long long> tprefix((size_t)n + 1);
-  uint64_t items = 0, trees = 0;
+  std::vector<uint32_t> cprefix((size_t)n + 1);
+  uint64_t items = 0, trees = 0, chunks = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
     prefix[(size_t)i] = (uint32_t)items;
     tprefix[(size_t)i] = trees;
+    cprefix[(size_t)i] = (uint32_t)chunks;
+    chunks += ntrees[i] == 0 ? 1 : (ntrees[i] + grt::kBinChunk - 1) / grt::kBinChunk;
     items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
     trees += ntrees[i];
     nt32[(size_t)i] = (uint32_t)ntrees[i];
@@ -282,20 +293,31 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   }
   prefix[(size_t)n] = (uint32_t)items;
   tprefix[(size_t)n] = trees;
+  cprefix[(size_t)n] = (uint32_t)chunks;
+  if (chunks > 0x7FFFFFFFull) return c->set_error(GRT_EINVAL, "too many binning chunks (total trees too large)");
   GRT_CUDA(c, cudaSetDevice(c->device));
   GRT_CUDA(c, p->prefix.ensure(prefix.size() * sizeof(uint32_t)));
   GRT_CUDA(c, p->tree_prefix.ensure(tprefix.size() * sizeof(unsigned long long)));
   GRT_CUDA(c, p->ntrees.ensure(nt32.size() * sizeof(uint32_t) + 4));
   GRT_CUDA(c, p->rec_w.ensure((size_t)trees * acc_size(c) + 16));
   GRT_CUDA(c, p->rec_o.ensure((size_t)trees + 16));
-  GRT_CUDA(c, p->work.ensure(64));
+  GRT_CUDA(c, p->chunk_prefix.ensure(cprefix.size() * sizeof(uint32_t)));
+  GRT_CUDA(c, p->part.ensure((size_t)chunks * 4 * (K + 2) * sizeof(double) + 16));
+  p->work_bytes = 64 + (((size_t)n * sizeof(uint32_t) + 63) & ~(size_t)63);
+  GRT_CUDA(c, p->work.ensure(p->work_bytes));
   GRT_CUDA(c, cudaMemcpy(p->prefix.ptr, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   GRT_CUDA(c, cudaMemcpy(p->tree_prefix.ptr, tprefix.data(), tprefix.size() * sizeof(unsigned long long),
                          cudaMemcpyHostToDevice));
   if (n > 0)
     GRT_CUDA(c, cudaMemcpy(p->ntrees.ptr, nt32.data(), nt32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  GRT_CUDA(c, cudaMemset(p->work.ptr, 0, 64));
+  GRT_CUDA(c, cudaMemcpy(p->chunk_prefix.ptr, cprefix.data(), cprefix.size() * sizeof(uint32_t),
+                         cudaMemcpyHostToDevice));
+  GRT_CUDA(c, cudaMemset(p->work.ptr, 0, p->work_bytes));
+  p->total_chunks = (uint32_t)chunks;
   p->n = n;
+  p->K = K;
+  p->L = L;
+  p->M = M;
   p->total_items = (uint32_t)items;
   p->total_trees = trees;
   p->host_ntrees.assign(ntrees, ntrees + n);
@@ -306,6 +328,7 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
 int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base, double *d_u,
                  double *d_coef, double *d_se, int32_t *d_status, cudaStream_t stream) {
   grt_ctx *c = p->ctx;
+  if (p->n < 0) return c->set_error(GRT_EINVAL, "plan has no valid layout (its last configuration failed)");
   if (p->n == 0) return GRT_OK;
   if (!d_x || !d_t || !d_u) return c->set_error(GRT_EINVAL, "x, t and u must be non-NULL");
   if (point_base + (uint64_t)p->n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
@@ -327,7 +350,7 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   w.stats = reinterpret_cast<unsigned long long *>(p->work.as<unsigned char>() + 8);
   const bool fp64 = c->pb.precision == GRT_FP64;
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[0], stream));
-  GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, 64, stream));
+  GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, p->work_bytes, stream));
   if (p->total_items > 0)
     GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[1], stream));
@@ -336,6 +359,10 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   f.rec_o = p->rec_o.as<uint8_t>();
   f.tree_prefix = p->tree_prefix.as<unsigned long long>();
   f.ntrees = p->ntrees.as<uint32_t>();
+  f.chunk_prefix = p->chunk_prefix.as<uint32_t>();
+  f.total_chunks = p->total_chunks;
+  f.part = p->part.as<double>();
+  f.done = reinterpret_cast<uint32_t *>(p->work.as<unsigned char>() + 64);
   f.n = (int)p->n;
   f.K = p->K;
   f.L = p->L;

@@ -15,7 +15,8 @@ namespace grt {
 constexpr int kMaxTerms = 16;     // powers 0..15 of f
 constexpr int kMaxK = 16;         // highest series order
 constexpr int kTile = 512;        // trees per work-queue chunk
-constexpr int kFinThreads = 128;  // threads of the finalize kernel (one block per point)
+constexpr int kFinThreads = 256;  // threads of a finalize (binning) block
+constexpr int kBinChunk = 4096;   // tree records binned by one finalize block
 constexpr int kWarpsPerBlock = 4; // persistent walk kernel
 constexpr unsigned kFull = 0xFFFFFFFFu;
 

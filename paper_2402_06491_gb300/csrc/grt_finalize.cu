@@ -115,22 +115,38 @@ __device__ double pade_value(const double *a, int L, int M, int *status) {
   return P / Q;
 }
 
-// One block per point.  Thread j bins the point's tree records j, j + T,
-// j + 2T, ... (T = kFinThreads) into its own column of per-order sums in
-// shared memory (S1 with Kahan compensation, S2, S|W|, counts); the columns
-// are then added in a fixed order.  The result depends only on the records.
+// Binning (Sec. 2.4: trees of order n give the n-th series coefficient).
+// One block per chunk of kBinChunk consecutive tree records of one point.
+// Thread j bins records j, j + T, j + 2T, ... of the chunk (T = kFinThreads)
+// into its own shared-memory column of per-order sums (S1 with Kahan
+// compensation, S2, S|W|, count); the columns are added in a fixed order and
+// the chunk's sums written to `part`.  The last block to finish a point
+// (fence + ticket, nobody waits) adds the point's chunk sums in chunk order,
+// forms a_n and SE_n and runs the FP64 Pade.  Every result depends only on
+// the records, not on block scheduling.
 template <typename Acc>
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeParams f) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int T = kFinThreads;
-  const int pt = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = f.K, R = K + 2;  // rows: orders 0..K and the pruned trees
+  const uint32_t chunk = blockIdx.x;
+  __shared__ int s_pt;
+  __shared__ bool s_last;
+  if (tid == 0) {  // point owning this chunk: largest p with chunk_prefix[p] <= chunk
+    int lo = 0, hi = f.n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (f.chunk_prefix[mid] <= chunk) lo = mid;
+      else hi = mid;
+    }
+    s_pt = lo;
+  }
   Acc *s1 = reinterpret_cast<Acc *>(smem);  // [R][T] each
   Acc *c1 = s1 + R * T;
   Acc *s2 = c1 + R * T;
   Acc *sa = s2 + R * T;
   uint32_t *cn = reinterpret_cast<uint32_t *>(sa + R * T);
-  __shared__ double tot[4][kMaxK + 2];
   for (int r = 0; r < R; ++r) {
     s1[r * T + tid] = Acc(0);
     c1[r * T + tid] = Acc(0);
@@ -138,11 +154,25 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
     sa[r * T + tid] = Acc(0);
     cn[r * T + tid] = 0u;
   }
-  const unsigned long long r0 = f.tree_prefix[pt], r1 = f.tree_prefix[pt + 1];
+  __syncthreads();
+  const int pt = s_pt;
+  const unsigned long long r0 = f.tree_prefix[pt] + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
+  const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, f.tree_prefix[pt + 1]);
   const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
-  for (unsigned long long i = r0 + tid; i < r1; i += T) {
-    const int o = f.rec_o[i];
-    const Acc w = rw[i];
+  constexpr int PER = kBinChunk / T;
+  int ord[PER];
+  Acc wv[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {  // all loads first, then the dependent updates
+    const unsigned long long i = r0 + (unsigned long long)(j * T + tid);
+    ord[j] = i < r1 ? (int)__ldcs(f.rec_o + i) : -1;
+    wv[j] = i < r1 ? __ldcs(rw + i) : Acc(0);
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int o = ord[j];
+    if (o < 0) continue;
+    const Acc w = wv[j];
     const int a = o * T + tid;
     if (o <= K) {
       kahan_add(s1[a], c1[a], w);
@@ -154,6 +184,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
   // columns l, l+32, ... with compensation, then a fixed butterfly over lanes
+  double *part = f.part + (size_t)chunk * 4 * R;
   for (int r = warp; r < R; r += T / 32) {
     Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
     unsigned long long ac = 0;
@@ -172,14 +203,32 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
       ac += __shfl_xor_sync(kFull, ac, off);
     }
     if (lane == 0) {
-      tot[0][r] = d1;
-      tot[1][r] = d2;
-      tot[2][r] = d3;
-      tot[3][r] = (double)ac;
+      part[r] = d1;
+      part[R + r] = d2;
+      part[2 * R + r] = d3;
+      part[3 * R + r] = (double)ac;
     }
   }
+  // publish this chunk; the point's last chunk to finish completes the point
+  __threadfence();
   __syncthreads();
+  if (tid == 0) {
+    const uint32_t nch = f.chunk_prefix[pt + 1] - f.chunk_prefix[pt];
+    s_last = atomicAdd(f.done + pt, 1u) == nch - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ double tot[4][kMaxK + 2];
   __shared__ double a[kMaxK + 1];
+  if (tid < 4 * R) {  // thread (stat, row) adds the point's chunk sums in chunk order
+    const double *pp = f.part + (size_t)f.chunk_prefix[pt] * 4 * R + tid;
+    const uint32_t nch = f.chunk_prefix[pt + 1] - f.chunk_prefix[pt];
+    double s = 0.0, c = 0.0;
+    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * 4 * R));
+    tot[tid / R][tid % R] = s - c;
+  }
+  __syncthreads();
   const double N = (double)f.ntrees[pt];
   if (tid <= K) {
     const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
@@ -219,7 +268,7 @@ template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParam
   const size_t smem = (size_t)(f.K + 2) * kFinThreads * (4 * sizeof(Acc) + sizeof(uint32_t));
   cudaError_t e = cudaFuncSetAttribute(finalize_kernel<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  finalize_kernel<Acc><<<f.n, kFinThreads, smem, stream>>>(f);
+  finalize_kernel<Acc><<<f.total_chunks, kFinThreads, smem, stream>>>(f);
   return cudaGetLastError();
 }
 

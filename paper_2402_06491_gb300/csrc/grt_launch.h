@@ -15,6 +15,10 @@ struct FinalizeParams {
   const uint8_t *rec_o;      // [total trees] tree orders (K+1 = pruned)
   const unsigned long long *tree_prefix;  // [n+1]
   const uint32_t *ntrees;    // [n]
+  const uint32_t *chunk_prefix;  // [n+1] first binning chunk of each point (every point has >= 1)
+  uint32_t total_chunks;
+  double *part;              // [chunks][4][K+2] per-chunk sums: S1, S2, S|W|, count
+  uint32_t *done;            // [n] chunks of each point finished (zeroed before the launch)
   int n, K, L, M;
   double *u;                 // [n]
   double *coef, *se;         // [n][K+1] or null
