@@ -241,10 +241,15 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
   default:
     break;
   }
+  // FP32 copy: exponent scales carry log2(e) (the FP32 walk evaluates e^v as 2^(v log2 e))
+  const double log2e = 1.4426950408889634;
   for (int i = 0; i < 8; ++i) {
     w.u0d[i] = c[i];
     w.u0f[i] = (float)c[i];
   }
+  if (pb.u0_kind == GRT_U0_GAUSS) w.u0f[2] = (float)(c[2] * log2e);
+  if (pb.u0_kind == GRT_U0_LOGISTIC) w.u0f[3] = (float)(c[3] * log2e);
+  w.lam_minus_cf = (float)(w.lam_minus_c * log2e);
   return GRT_OK;
 }
 

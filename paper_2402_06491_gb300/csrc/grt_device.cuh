@@ -106,6 +106,34 @@ template <> struct Math<double> {
   static __device__ __forceinline__ double cospi(double v) { return ::cospi(v); }
 };
 
+// Node-body arithmetic.  The FP32 walk uses the special-function unit:
+//   -2 ln U       = -2 ln 2 * lg2(U)                    (MUFU.LG2)
+//   sin, cos(2 pi U) from sin/cos of 2 pi (U - 1/2) in [-pi, pi), negated
+//   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ)
+//   e^v           = 2^(v log2 e), the log2 e folded into the caller's constant
+// each within a few units in the last place of binary32 on these ranges (the
+// error of lg2 near U = 1 is absolute, ~2^-22, and only moves rare, tiny
+// normals).  The FP64 walk uses the correctly-rounded library functions.
+template <typename Real> struct Node;
+template <> struct Node<float> {
+  static __device__ __forceinline__ float neg2ln(float u) { return -1.3862943611198906f * __log2f(u); }
+  static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) {
+    const float th = 6.2831853071795865f * (u - 0.5f);
+    *s = -__sinf(th);
+    *c = -__cosf(th);
+  }
+  static __device__ __forceinline__ float cos2pi(float u) { return -__cosf(6.2831853071795865f * (u - 0.5f)); }
+  static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
+  static __device__ __forceinline__ float exp_scaled(float v) { return exp2f(v); }  // v already times log2 e
+};
+template <> struct Node<double> {
+  static __device__ __forceinline__ double neg2ln(double u) { return -2.0 * ::log(u); }
+  static __device__ __forceinline__ void sincos2pi(double u, double *s, double *c) { ::sincospi(2.0 * u, s, c); }
+  static __device__ __forceinline__ double cos2pi(double u) { return ::cospi(2.0 * u); }
+  static __device__ __forceinline__ double sqrt_pos(double v) { return ::sqrt(v); }
+  static __device__ __forceinline__ double exp_scaled(double v) { return ::exp(v); }  // v is the plain exponent
+};
+
 template <typename Real> __device__ __forceinline__ Real pconst(const WalkParams &p, int i);
 template <> __device__ __forceinline__ float pconst<float>(const WalkParams &p, int i) { return p.u0f[i]; }
 template <> __device__ __forceinline__ double pconst<double>(const WalkParams &p, int i) { return p.u0d[i]; }
@@ -133,7 +161,8 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
   }
 }
 
-// Initial data g at x_p + D.  Constants (host-prepared):
+// Initial data g at x_p + D.  Constants (host-prepared; the exponent scales
+// carry a factor log2 e in the FP32 copy, see Node<float>::exp_scaled):
 //   GAUSS     c0, A, -1/(2 s^2), x0, y0, z0
 //   COS_PROD  c0, A, w0, w1, w2
 //   TANH_PROD c0, A, s0, s1, s2
@@ -150,7 +179,7 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&b
       const Real e = base[i] + D[i];
       r2 += e * e;
     }
-    return c0 + A * M::exp(r2 * pconst<Real>(p, 2));
+    return c0 + A * Node<Real>::exp_scaled(r2 * pconst<Real>(p, 2));
   }
   case kU0CosProd: {
     Real pr = Real(1);
@@ -165,7 +194,7 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&b
     return c0 + A * pr;
   }
   case kU0Logistic:
-    return c0 + A / (Real(1) + M::exp((base[0] + D[0]) * pconst<Real>(p, 3)));
+    return c0 + A / (Real(1) + Node<Real>::exp_scaled((base[0] + D[0]) * pconst<Real>(p, 3)));
   default:
     return c0;
   }
@@ -218,19 +247,20 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   using M = Math<Real>;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree, point), p.rk0, p.rk1);
   // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
+  using F = Node<Real>;
   Real n[DIM];
   {
-    const Real r = M::sqrt(Real(-2) * M::log(uniform01<Real>(w.z)));
+    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z)));
     Real s, c;
-    M::sincospi(Real(2) * uniform01<Real>(w.w), &s, &c);
+    F::sincos2pi(uniform01<Real>(w.w), &s, &c);
     n[0] = r * c;
     if (DIM > 1) n[DIM > 1 ? 1 : 0] = r * s;
   }
   if (DIM == 3) {
     const uint4 w2 = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree | 0x80000000u, point),
                                    p.rk0, p.rk1);
-    const Real r = M::sqrt(Real(-2) * M::log(uniform01<Real>(w2.x)));
-    n[DIM - 1] = r * M::cospi(Real(2) * uniform01<Real>(w2.y));
+    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w2.x)));
+    n[DIM - 1] = r * F::cos2pi(uniform01<Real>(w2.y));
   }
 
   bool leaf;
@@ -243,13 +273,13 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     seg = leaf ? tau : tau * S;
     o.tau_c = tau * (Real(1) - S);
   } else {
-    S = -M::log(uniform01<Real>(w.x)) * Scalars<Real>::inv_lambda(p);
+    S = Real(0.5) * F::neg2ln(uniform01<Real>(w.x)) * Scalars<Real>::inv_lambda(p);
     leaf = (S >= tau) || (p.nterms == 0);
     seg = leaf ? tau : S;
     o.tau_c = tau - S;
     o.cat = leaf ? -1 : categorical(s_thr, w.y, 0, p.ncat_thr);
   }
-  const Real sc = M::sqrt(Scalars<Real>::two_D(p) * seg);
+  const Real sc = F::sqrt_pos(Scalars<Real>::two_D(p) * seg);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
 
@@ -259,7 +289,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
       o.factor = (Real)p.leaf_factor * g;
     } else {
       const Real lmc = Scalars<Real>::lam_minus_c(p);
-      o.factor = (lmc == Real(0)) ? g : M::exp(lmc * tau) * g;
+      o.factor = (lmc == Real(0)) ? g : F::exp_scaled(lmc * tau) * g;
     }
   } else {
     const Real tf = s_factor[o.cat];
@@ -267,7 +297,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
       o.factor = tau * tf;
     } else {
       const Real lmc = Scalars<Real>::lam_minus_c(p);
-      o.factor = (lmc == Real(0)) ? tf : M::exp(lmc * S) * tf;
+      o.factor = (lmc == Real(0)) ? tf : F::exp_scaled(lmc * S) * tf;
     }
   }
 }

@@ -187,14 +187,16 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   double *part = f.part + (size_t)chunk * 4 * R;
   for (int r = warp; r < R; r += T / 32) {
     Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
-    unsigned long long ac = 0;
+    uint32_t ac = 0;
     for (int j = lane; j < T; j += 32) {
       kahan_add(a1, k1, s1[r * T + j] - c1[r * T + j]);
       kahan_add(a2, k2, s2[r * T + j]);
       kahan_add(a3, k3, sa[r * T + j]);
       ac += cn[r * T + j];
     }
-    double d1 = (double)a1 - (double)k1, d2 = (double)a2 - (double)k2, d3 = (double)a3 - (double)k3;
+    // butterfly in the walk's precision (FP64 arithmetic is scarce on this GPU:
+    // it is used once per row, for the conversion)
+    Acc d1 = a1 - k1, d2 = a2 - k2, d3 = a3 - k3;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       d1 += __shfl_xor_sync(kFull, d1, off);
@@ -203,9 +205,9 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
       ac += __shfl_xor_sync(kFull, ac, off);
     }
     if (lane == 0) {
-      part[r] = d1;
-      part[R + r] = d2;
-      part[2 * R + r] = d3;
+      part[r] = (double)d1;
+      part[R + r] = (double)d2;
+      part[2 * R + r] = (double)d3;
       part[3 * R + r] = (double)ac;
     }
   }
