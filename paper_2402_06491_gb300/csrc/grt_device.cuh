@@ -15,8 +15,8 @@ namespace grt {
 constexpr int kMaxTerms = 16;     // powers 0..15 of f
 constexpr int kMaxK = 16;         // highest series order
 constexpr int kTile = 512;        // trees per work-queue chunk
-constexpr int kFinThreads = 256;  // threads of a finalize (binning) block
-constexpr int kBinChunk = 4096;   // tree records binned by one finalize block
+constexpr int kFinThreads = 128;  // threads of a finalize (binning) block
+constexpr int kBinChunk = 8192;   // tree records binned by one finalize block
 constexpr int kWarpsPerBlock = 4; // persistent walk kernel
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -106,23 +106,20 @@ template <> struct Math<double> {
   static __device__ __forceinline__ double cospi(double v) { return ::cospi(v); }
 };
 
-// Node-body arithmetic.  The FP32 walk uses the special-function unit:
+// Node-body arithmetic.  The FP32 walk uses the special-function unit where
+// its accuracy holds on the argument range:
 //   -2 ln U       = -2 ln 2 * lg2(U)                    (MUFU.LG2)
-//   sin, cos(2 pi U) from sin/cos of 2 pi (U - 1/2) in [-pi, pi), negated
 //   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ)
 //   e^v           = 2^(v log2 e), the log2 e folded into the caller's constant
-// each within a few units in the last place of binary32 on these ranges (the
-// error of lg2 near U = 1 is absolute, ~2^-22, and only moves rare, tiny
-// normals).  The FP64 walk uses the correctly-rounded library functions.
+// (the error of lg2 near U = 1 is absolute, ~2^-22, and only moves rare, tiny
+// normals).  sin and cos of 2 pi U use the accurate sincospi: the SFU's
+// absolute error (~2^-21) on the normals shows up in u0 near its zeros.  The
+// FP64 walk uses the library functions throughout.
 template <typename Real> struct Node;
 template <> struct Node<float> {
   static __device__ __forceinline__ float neg2ln(float u) { return -1.3862943611198906f * __log2f(u); }
-  static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) {
-    const float th = 6.2831853071795865f * (u - 0.5f);
-    *s = -__sinf(th);
-    *c = -__cosf(th);
-  }
-  static __device__ __forceinline__ float cos2pi(float u) { return -__cosf(6.2831853071795865f * (u - 0.5f)); }
+  static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+  static __device__ __forceinline__ float cos2pi(float u) { return cospif(2.0f * u); }
   static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
   static __device__ __forceinline__ float exp_scaled(float v) { return exp2f(v); }  // v already times log2 e
 };

@@ -159,27 +159,29 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   const unsigned long long r0 = f.tree_prefix[pt] + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
   const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, f.tree_prefix[pt + 1]);
   const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
-  constexpr int PER = kBinChunk / T;
-  int ord[PER];
-  Acc wv[PER];
+  constexpr int BATCH = 16;  // records in flight per thread
+  for (int b0 = 0; b0 < kBinChunk; b0 += BATCH * T) {
+    int ord[BATCH];
+    Acc wv[BATCH];
 #pragma unroll
-  for (int j = 0; j < PER; ++j) {  // all loads first, then the dependent updates
-    const unsigned long long i = r0 + (unsigned long long)(j * T + tid);
-    ord[j] = i < r1 ? (int)__ldcs(f.rec_o + i) : -1;
-    wv[j] = i < r1 ? __ldcs(rw + i) : Acc(0);
-  }
-#pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    const int o = ord[j];
-    if (o < 0) continue;
-    const Acc w = wv[j];
-    const int a = o * T + tid;
-    if (o <= K) {
-      kahan_add(s1[a], c1[a], w);
-      s2[a] += w * w;
-      sa[a] += w < Acc(0) ? -w : w;
+    for (int j = 0; j < BATCH; ++j) {  // all loads of the batch first, then the dependent updates
+      const unsigned long long i = r0 + (unsigned long long)(b0 + j * T + tid);
+      ord[j] = i < r1 ? (int)__ldcs(f.rec_o + i) : -1;
+      wv[j] = i < r1 ? __ldcs(rw + i) : Acc(0);
     }
-    cn[a] += 1u;
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int o = ord[j];
+      if (o < 0) continue;
+      const Acc w = wv[j];
+      const int a = o * T + tid;
+      if (o <= K) {
+        kahan_add(s1[a], c1[a], w);
+        s2[a] += w * w;
+        sa[a] += w < Acc(0) ? -w : w;
+      }
+      cn[a] += 1u;
+    }
   }
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
