@@ -418,31 +418,35 @@ int oracle_trees(const or_problem *pb, const double *x, double t, uint64_t point
 /*   i = 1..M (c_{<0} = 0); numerator alpha_i = sum_{j<=min(i,M)} beta_j    */
 /*   c_{i-j}.  Solved on c_n = a_n / rho^n and evaluated at w = rho, which  */
 /*   equals the unscaled approximant at eps = 1 (a Pade approximant is      */
-/*   invariant under eps -> s eps; the paper fixes no scaling).  A pivot    */
-/*   below 1e-14 times the largest matrix entry lowers the type to          */
-/*   [L-1/M-1] (L stays >= 0).                                              */
+/*   invariant under eps -> s eps; the paper fixes no scaling; rho is a     */
+/*   power of two, so the rescaling itself is exact).  A pivot below 1e-14  */
+/*   times the largest matrix entry lowers the type to [L-1/M-1] (L stays   */
+/*   >= 0).                                                                 */
 /* ------------------------------------------------------------------------ */
 int oracle_pade(int L, int M, const double *a, double *u_out, int32_t *status_out, int32_t *lm_used)
 {
     int32_t status = 0;
     if (L < 0 || M < 0 || L + M > OR_MAX_K) return -1;
     int n = L + M;
-    /* Scale: rho = max_{j > m} (|a_j| / |a_m|)^{1/(j-m)}, m the first nonzero
-     * coefficient (the root test's growth rate), so that |c_j| <= |c_m| for all j
-     * and the fastest-growing coefficient matches |c_m|.  rho = 1 when no two
-     * coefficients are nonzero. */
-    double rho = 0.0;
+    /* Scale: rho = 2^k with k the integer growth rate of the binary exponents,
+     * k = max_{j > m} ceil((e_j - e_m) / (j - m)), e_j = ilogb(a_j), m the first
+     * nonzero coefficient: a root-test estimate rounded to a power of two, so
+     * that c_j = a_j 2^{-k j} is exact and |c_j| < 2^{e_m - k m + 1}.  k = 0 when
+     * no two coefficients are nonzero. */
     int m = 0;
     while (m <= n && a[m] == 0.0) ++m;
+    int k = 0, have = 0;
     for (int j = m + 1; j <= n; ++j)
         if (a[j] != 0.0) {
-            double r = pow(fabs(a[j]) / fabs(a[m]), 1.0 / (double)(j - m));
-            if (r > rho) rho = r;
+            int num = ilogb(a[j]) - ilogb(a[m]), den = j - m;
+            int q = num / den;
+            if (num % den != 0 && num > 0) q += 1; /* ceiling for positive, C truncation is the ceiling for negative */
+            if (!have || q > k) k = q;
+            have = 1;
         }
-    if (!(rho > 0.0) || !isfinite(rho)) rho = 1.0;
+    double rho = ldexp(1.0, k);
     double c[OR_MAX_K + 1];
-    for (int i = 0; i <= n; ++i) c[i] = a[i] / pow(rho, (double)i);
-
+    for (int i = 0; i <= n; ++i) c[i] = ldexp(a[i], -k * i);
     int Lc = L, Mc = M;
     double beta[OR_MAX_K + 1];
     for (;;) {

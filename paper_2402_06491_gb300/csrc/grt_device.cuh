@@ -108,16 +108,15 @@ template <> struct Math<double> {
 
 // Node-body arithmetic.  The FP32 walk uses the special-function unit where
 // its accuracy holds on the argument range:
-//   -2 ln U       = -2 ln 2 * lg2(U)                    (MUFU.LG2)
-//   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ)
+//   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ, ~2 ulp)
 //   e^v           = 2^(v log2 e), the log2 e folded into the caller's constant
-// (the error of lg2 near U = 1 is absolute, ~2^-22, and only moves rare, tiny
-// normals).  sin and cos of 2 pi U use the accurate sincospi: the SFU's
-// absolute error (~2^-21) on the normals shows up in u0 near its zeros.  The
-// FP64 walk uses the library functions throughout.
+// ln U and sin / cos of 2 pi U use the accurate library functions: the SFU's
+// absolute error (~2^-22) becomes a large relative error of -2 ln U for U
+// near 1 and of the normals, which shows up in u0 near its zeros.  The FP64
+// walk uses the library functions throughout.
 template <typename Real> struct Node;
 template <> struct Node<float> {
-  static __device__ __forceinline__ float neg2ln(float u) { return -1.3862943611198906f * __log2f(u); }
+  static __device__ __forceinline__ float neg2ln(float u) { return -2.0f * logf(u); }
   static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
   static __device__ __forceinline__ float cos2pi(float u) { return cospif(2.0f * u); }
   static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }

@@ -22,26 +22,33 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double v) {
 }
 
 // [L/M] Pade of sum a_n eps^n at eps = 1.  The series is first rescaled,
-// c_n = a_n / rho^n with rho = max_{j > m} (|a_j| / |a_m|)^{1/(j-m)} (m the
-// first nonzero term), which leaves the approximant unchanged (evaluated at
-// w = rho) and bounds every |c_j| by |c_m| in the Toeplitz system
+// c_n = a_n / rho^n with rho = 2^k, k = max_{j > m} ceil((e_j - e_m)/(j - m)),
+// e_j the binary exponent of a_j and m the first nonzero term: this leaves the
+// approximant unchanged (evaluated at w = rho), is exact in floating point,
+// needs no transcendental function, and keeps every |c_j| within a factor of
+// two of |c_m| or below in the Toeplitz system
 // sum_{j=1..M} c_{L+i-j} beta_j = -c_{L+i}, i = 1..M.  Gaussian
 // elimination with partial pivoting; a pivot at or below 1e-14 times the
 // largest entry lowers the type to [L-1/M-1] (L not below 0) and sets
 // PADE_SINGULAR.  |Q(1)| < 1e-8 sets PADE_POLE_NEAR.
 __device__ double pade_value(const double *a, int L, int M, int *status) {
   const int n = L + M;
-  // growth rate of the series by the root test, relative to its first nonzero term
+  // growth rate of the series by the root test on its binary exponents,
+  // rounded up to an integer: rho = 2^k, so the rescaling below is exact
   int first = 0;
   while (first <= n && a[first] == 0.0) ++first;
-  double rho = 0.0;
+  int k = 0;
+  bool any = false;
   for (int j = first + 1; j <= n; ++j) {
     if (a[j] == 0.0) continue;
-    rho = fmax(rho, pow(fabs(a[j]) / fabs(a[first]), 1.0 / (double)(j - first)));
+    const int num = ilogb(a[j]) - ilogb(a[first]), den = j - first;
+    const int q = num > 0 ? (num + den - 1) / den : -((-num) / den);  // ceil(num / den)
+    k = any ? max(k, q) : q;
+    any = true;
   }
-  if (!(rho > 0.0) || !isfinite(rho)) rho = 1.0;
+  const double rho = scalbn(1.0, k);
   double c[kMaxK + 1];
-  for (int i = 0; i <= n; ++i) c[i] = a[i] / pow(rho, (double)i);
+  for (int i = 0; i <= n; ++i) c[i] = scalbn(a[i], -k * i);
 
   int st = 0;
   int Lc = L, Mc = M;
@@ -159,16 +166,20 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   const unsigned long long r0 = f.tree_prefix[pt] + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
   const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, f.tree_prefix[pt + 1]);
   const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
-  constexpr int BATCH = 16;  // records in flight per thread
-  for (int b0 = 0; b0 < kBinChunk; b0 += BATCH * T) {
-    int ord[BATCH];
-    Acc wv[BATCH];
+  constexpr int BATCH = 8;  // records per thread per batch; the next batch is in flight meanwhile
+  constexpr int STEP = BATCH * T;
+  int oa[BATCH], ob[BATCH];
+  Acc wa[BATCH], wb[BATCH];
+  auto load = [&](int (&ord)[BATCH], Acc (&wv)[BATCH], int b0) {
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) {  // all loads of the batch first, then the dependent updates
+    for (int j = 0; j < BATCH; ++j) {
       const unsigned long long i = r0 + (unsigned long long)(b0 + j * T + tid);
-      ord[j] = i < r1 ? (int)__ldcs(f.rec_o + i) : -1;
-      wv[j] = i < r1 ? __ldcs(rw + i) : Acc(0);
+      const bool in = b0 < kBinChunk && i < r1;
+      ord[j] = in ? (int)__ldcs(f.rec_o + i) : -1;
+      wv[j] = in ? __ldcs(rw + i) : Acc(0);
     }
+  };
+  auto bin = [&](const int (&ord)[BATCH], const Acc (&wv)[BATCH]) {
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) {
       const int o = ord[j];
@@ -182,6 +193,15 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
       }
       cn[a] += 1u;
     }
+  };
+  const int span = (int)min((unsigned long long)kBinChunk, r1 - r0);  // records of this chunk
+  load(oa, wa, 0);
+#pragma unroll 1
+  for (int b0 = 0; b0 < span; b0 += 2 * STEP) {
+    load(ob, wb, b0 + STEP);
+    bin(oa, wa);
+    load(oa, wa, b0 + 2 * STEP);
+    bin(ob, wb);
   }
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
@@ -213,8 +233,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
       part[3 * R + r] = (double)ac;
     }
   }
-  // publish this chunk; the point's last chunk to finish completes the point
-  __threadfence();
+  // publish this chunk (its writers fence); the point's last chunk to finish completes the point
+  if (lane == 0) __threadfence();
   __syncthreads();
   if (tid == 0) {
     const uint32_t nch = f.chunk_prefix[pt + 1] - f.chunk_prefix[pt];
