@@ -129,11 +129,17 @@ def test_kpp_1d_full_workload_fp64(grt):
     assert np.array_equal(g["status"], o["status"])
 
 
-@pytest.mark.parametrize("name,ntrees", [("sin_2d", 2600), ("pdd_3d", 1500), ("uneven_2d", 3000)])
-def test_point_solve_fp32(grt, name, ntrees):
+# Coefficient budget: 3e-5 of the mean |W| of the order where u0 keeps its sign.
+# pdd_3d's u0 = prod tanh(x_i - 2) changes sign on the interface planes; near
+# its zeros the relative error of g is set by the FP32 rounding of the position
+# (~2^-24 (|x_p - 2| + |D|) absolute), not by a few ulp, so a high order with a
+# handful of trees gets up to ~1e-4: budget 1.5e-4 there (the Pade bar is the same).
+@pytest.mark.parametrize("name,ntrees,ctol", [("sin_2d", 2600, 3e-5), ("pdd_3d", 1500, 1.5e-4),
+                                              ("uneven_2d", 3000, 3e-5)])
+def test_point_solve_fp32(grt, name, ntrees, ctol):
     wl = workloads.subsample(workloads.WORKLOADS[name](), 24, ntrees=ntrees)
     g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
-    _assert_fp32_parity(g, o, wl["ntrees"])
+    _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol)
 
 
 def test_edge_budgets_and_orders(grt):
