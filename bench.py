@@ -40,6 +40,24 @@ SM_COUNT_GB300 = 152
 ISSUE_PER_SM_PER_CLK = 4 * 32   # 4 schedulers x 1 warp-instruction x 32 threads
 
 
+def _walk_traffic():
+    """DRAM bytes per full-size walk launch from the committed ncu summary, or None when the
+    walk kernel's sources changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", "walk_kernel_sin2d.md")).read()
+        want = re.search(r"source_sha256_16: ([0-9a-f]+)", text).group(1)
+        traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+        h = hashlib.sha256()
+        for f in ("grt_device.cuh", "grt_walk.cu"):
+            with open(os.path.join(ROOT, "paper_2402_06491_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        return traffic if h.hexdigest()[:16] == want else None
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -387,7 +405,9 @@ def gpu_arm(args) -> int:
         },
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": _walk_traffic() if not args.trees else None,
+            "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md); "
+                            "algorithmic bytes are the 5 B/tree records = 256 MB written",
             "kernel": "walk_kernel<float,2,B> (persistent tree walk)",
             "work": f"{inst:.4g} algorithmic thread-instructions per launch = {model['node']}/node x {nodes} nodes"
                     f" + {model['leaf']}/leaf x {nodes - splits} + {model['split']}/split x {splits}"
