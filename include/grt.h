@@ -186,6 +186,30 @@ int grt_pade(grt_ctx *ctx, int64_t n, int K, int L, int M, const double *coef, d
 int grt_trees(grt_ctx *ctx, const double *x, double t, uint64_t point_index, uint64_t first_tree, uint64_t ntrees,
               int K, uint64_t seed, int32_t *order, double *w, uint32_t *nodes, uint64_t *hash);
 
+/* Limits of grt_solve_noalloc. */
+#define GRT_NOALLOC_MAX_POINTS 4096
+#define GRT_NOALLOC_MAX_TREES 524288ull /* summed over the call's points */
+
+/* Point solve that allocates no memory (the paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory when they solve,
+ * e.g. code running under a CUDA stream capture, where cudaMalloc is not
+ * allowed, or an application whose own pool allocator owns the device memory).
+ * Same arguments and results as grt_plan_execute, without a plan: d_x [n][dim],
+ * d_t [n], d_u [n], d_coef / d_se [n][K+1] (may be NULL), d_status [n] (may be
+ * NULL) are DEVICE arrays owned by the caller; ntrees [n] is a HOST array.  The
+ * work area of the solve is one fixed array of about 7 MB of device memory
+ * that the library holds on every GPU that loads it until the process exits.
+ * Limits: n <= GRT_NOALLOC_MAX_POINTS and sum(ntrees) <= GRT_NOALLOC_MAX_TREES,
+ * else GRT_EINVAL with a message.  The first call on a device looks up the
+ * work area's device address; make that first call before any stream capture.
+ * Enqueued on `stream` (NULL = legacy default stream); returns after enqueueing.
+ * All calls share the one work area: calls whose GPU work can overlap in time
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller. */
+int grt_solve_noalloc(grt_ctx *ctx, int64_t n, const double *d_x, const double *d_t, const uint64_t *ntrees, int K,
+                      int L, int M, uint64_t seed, uint64_t point_base, double *d_u, double *d_coef, double *d_se,
+                      int32_t *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ def _load():
         "grt_plan_destroy": ([_vp], None),
         "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
+        "grt_solve_noalloc": ([_vp, i64, _vp, _vp, u64p, i32, i32, i32, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -319,6 +320,28 @@ def grt_trees(ctx: Context, x, t: float, point_index: int, first_tree: int, ntre
     return dict(order=order, w=w, nodes=nodes, hash=h)
 
 
+NOALLOC_MAX_POINTS = 4096
+NOALLOC_MAX_TREES = 524288
+
+
+def grt_solve_noalloc(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int, point_base: int, u, coef=None,
+                      se=None, status=None, stream=None) -> None:
+    """Point solve that allocates no device memory (for callers that cannot allocate when they solve).
+
+    x, t, u, coef, se, status are the caller's device buffers (torch CUDA tensors or raw
+    addresses); ntrees is a host array.  The solve's work area is a fixed ~7 MB array the
+    library keeps on the device; calls whose GPU work overlaps in time race on it.
+    """
+    lib = _load()
+    nt = np.ascontiguousarray(np.asarray(ntrees, np.uint64).reshape(-1))
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.grt_solve_noalloc(ctx.handle, nt.size, _devptr(x), _devptr(t), _ptr(nt, ctypes.c_uint64), K, L, M,
+                               int(seed), int(point_base), _devptr(u), _devptr(coef), _devptr(se), _devptr(status), sh)
+    _check(rc, ctx.handle)
+
+
 EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
-            "grt_pade", "grt_trees"]
+            "grt_pade", "grt_trees", "grt_solve_noalloc"]

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -649,3 +650,144 @@ int grt_trees(grt_ctx *c, const double *x, double t, uint64_t point_index, uint6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without any device allocation (grt_solve_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need a solve:
+// code running under a CUDA stream capture (cudaMalloc is not capturable), or
+// a host that has handed all device memory to its own pool allocator.  For
+// them the whole work area of a solve lives in one fixed-size array of device
+// memory that belongs to the library (every GPU that loads it holds the array
+// until the process exits).  The array is shared by every call, so calls whose
+// GPU work overlaps in time race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocWorkBytes = 64 + (size_t)GRT_NOALLOC_MAX_POINTS * sizeof(uint32_t);
+constexpr size_t kNoAllocMaxChunks =
+    (size_t)GRT_NOALLOC_MAX_POINTS + (size_t)GRT_NOALLOC_MAX_TREES / grt::kBinChunk;
+
+constexpr size_t na_align(size_t v) { return (v + 255) & ~(size_t)255; }
+// byte offsets of the pieces of the work area
+constexpr size_t kNaWork = 0;
+constexpr size_t kNaPrefix = na_align(kNaWork + kNoAllocWorkBytes);
+constexpr size_t kNaTreePrefix = na_align(kNaPrefix + (GRT_NOALLOC_MAX_POINTS + 1) * sizeof(uint32_t));
+constexpr size_t kNaNtrees = na_align(kNaTreePrefix + (GRT_NOALLOC_MAX_POINTS + 1) * sizeof(unsigned long long));
+constexpr size_t kNaChunkPrefix = na_align(kNaNtrees + GRT_NOALLOC_MAX_POINTS * sizeof(uint32_t));
+constexpr size_t kNaRecO = na_align(kNaChunkPrefix + (GRT_NOALLOC_MAX_POINTS + 1) * sizeof(uint32_t));
+constexpr size_t kNaRecW = na_align(kNaRecO + GRT_NOALLOC_MAX_TREES);
+constexpr size_t kNaPart = na_align(kNaRecW + (size_t)GRT_NOALLOC_MAX_TREES * sizeof(double));
+constexpr size_t kNaBytes = na_align(kNaPart + kNoAllocMaxChunks * 4 * (GRT_MAX_K + 2) * sizeof(double));
+
+// The library's fixed work area (about 7 MB).  Host code must not use this
+// name as an address: it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNaMaxDevices] = {};
+
+// Device address of the work area on the current device `dev`, looked up once
+// per device (on the first call of grt_solve_noalloc on that device).
+cudaError_t noalloc_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char *>(g_noalloc_ptr[dev]);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const double *d_t, const uint64_t *ntrees,
+                                 int K, int L, int M, uint64_t seed, uint64_t point_base, double *d_u, double *d_coef,
+                                 double *d_se, int32_t *d_status, void *stream_handle) {
+  if (!c) return GRT_EINVAL;
+  if (n < 0) return c->set_error(GRT_EINVAL, "n must be >= 0");
+  if (n > GRT_NOALLOC_MAX_POINTS)
+    return c->set_error(GRT_EINVAL, "grt_solve_noalloc: n above GRT_NOALLOC_MAX_POINTS (4096)");
+  if (K < 0 || K > GRT_MAX_K) return c->set_error(GRT_EINVAL, "K must be in [0, 16]");
+  if (L < 0 || M < 0 || L + M > K) return c->set_error(GRT_EINVAL, "need L, M >= 0 and L + M <= K");
+  if (n == 0) return GRT_OK;
+  if (!ntrees || !d_x || !d_t || !d_u) return c->set_error(GRT_EINVAL, "x, t, ntrees and u must be non-NULL");
+  if (point_base + (uint64_t)n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
+  // work layout on the host, in fixed-size arrays on this thread's stack (no heap)
+  uint32_t prefix[GRT_NOALLOC_MAX_POINTS + 1], nt32[GRT_NOALLOC_MAX_POINTS], cprefix[GRT_NOALLOC_MAX_POINTS + 1];
+  unsigned long long tprefix[GRT_NOALLOC_MAX_POINTS + 1];
+  uint64_t items = 0, trees = 0, chunks = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
+    prefix[i] = (uint32_t)items;
+    tprefix[i] = trees;
+    cprefix[i] = (uint32_t)chunks;
+    nt32[i] = (uint32_t)ntrees[i];
+    items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
+    chunks += ntrees[i] == 0 ? 1 : (ntrees[i] + grt::kBinChunk - 1) / grt::kBinChunk;
+    trees += ntrees[i];
+    if (trees > GRT_NOALLOC_MAX_TREES)
+      return c->set_error(GRT_EINVAL, "grt_solve_noalloc: total trees above GRT_NOALLOC_MAX_TREES (524288)");
+  }
+  prefix[n] = (uint32_t)items;
+  tprefix[n] = trees;
+  cprefix[n] = (uint32_t)chunks;
+
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  unsigned char *base = nullptr;
+  GRT_CUDA(c, noalloc_scratch(c->device, &base));
+  cudaStream_t stream = (cudaStream_t)stream_handle;
+  const size_t nn = (size_t)n;
+  GRT_CUDA(c, cudaMemcpyAsync(base + kNaPrefix, prefix, (nn + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  GRT_CUDA(c, cudaMemcpyAsync(base + kNaTreePrefix, tprefix, (nn + 1) * sizeof(unsigned long long),
+                              cudaMemcpyHostToDevice, stream));
+  GRT_CUDA(c, cudaMemcpyAsync(base + kNaNtrees, nt32, nn * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  GRT_CUDA(c, cudaMemcpyAsync(base + kNaChunkPrefix, cprefix, (nn + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                              stream));
+  // what must start at zero: queue head, counters, the per-point chunk tickets
+  GRT_CUDA(c, cudaMemsetAsync(base + kNaWork, 0, 64 + nn * sizeof(uint32_t), stream));
+
+  grt::WalkParams w = c->base;
+  set_round_keys(w, seed);
+  w.K = K;
+  w.point_base = (uint32_t)point_base;
+  w.x = d_x;
+  w.t = d_t;
+  w.ntrees = reinterpret_cast<const uint32_t *>(base + kNaNtrees);
+  w.prefix = reinterpret_cast<const uint32_t *>(base + kNaPrefix);
+  w.tree_prefix = reinterpret_cast<const unsigned long long *>(base + kNaTreePrefix);
+  w.n = (int)n;
+  w.total_items = (uint32_t)items;
+  w.rec_w = base + kNaRecW;
+  w.rec_o = base + kNaRecO;
+  w.counter = reinterpret_cast<uint32_t *>(base + kNaWork);
+  w.stats = reinterpret_cast<unsigned long long *>(base + kNaWork + 8);
+  const bool fp64 = c->pb.precision == GRT_FP64;
+  if (items > 0)
+    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
+  grt::FinalizeParams f{};
+  f.rec_w = w.rec_w;
+  f.rec_o = w.rec_o;
+  f.tree_prefix = w.tree_prefix;
+  f.ntrees = w.ntrees;
+  f.chunk_prefix = reinterpret_cast<const uint32_t *>(base + kNaChunkPrefix);
+  f.total_chunks = (uint32_t)chunks;
+  f.part = reinterpret_cast<double *>(base + kNaPart);
+  f.done = reinterpret_cast<uint32_t *>(base + kNaWork + 64);
+  f.n = (int)n;
+  f.K = K;
+  f.L = L;
+  f.M = M;
+  f.u = d_u;
+  f.coef = d_coef;
+  f.se = d_se;
+  f.status = d_status;
+  f.stats = w.stats;
+  GRT_CUDA(c, grt::launch_finalize(fp64, f, stream));
+  return GRT_OK;
+}
