@@ -206,6 +206,7 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
       }
     }
   }
+  w.leaf_factorf = (float)w.leaf_factor;
   // finite thresholds: all before the first that reaches 2^32
   int nfin = 0;
   while (nfin < ncat - 1 && T[nfin] < 4294967296ull) ++nfin;

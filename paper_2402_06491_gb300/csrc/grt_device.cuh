@@ -32,6 +32,7 @@ struct WalkParams {
   int arity[kMaxTerms];
   double term_factor[kMaxTerms];  // B: b_k / P(k);  A: b_k / (lambda P(k))
   double leaf_factor;             // B: 1 / P(leaf)
+  float leaf_factorf;             // the same in binary32 (the FP32 walk converts nothing per node)
   // problem scalars
   int u0_kind;
   int K;
@@ -198,11 +199,13 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&b
 
 template <typename Real> struct Scalars;
 template <> struct Scalars<float> {
+  static __device__ __forceinline__ float leaf(const WalkParams &p) { return p.leaf_factorf; }
   static __device__ __forceinline__ float two_D(const WalkParams &p) { return p.two_Df; }
   static __device__ __forceinline__ float inv_lambda(const WalkParams &p) { return p.inv_lambdaf; }
   static __device__ __forceinline__ float lam_minus_c(const WalkParams &p) { return p.lam_minus_cf; }
 };
 template <> struct Scalars<double> {
+  static __device__ __forceinline__ double leaf(const WalkParams &p) { return p.leaf_factor; }
   static __device__ __forceinline__ double two_D(const WalkParams &p) { return p.two_D; }
   static __device__ __forceinline__ double inv_lambda(const WalkParams &p) { return p.inv_lambda; }
   static __device__ __forceinline__ double lam_minus_c(const WalkParams &p) { return p.lam_minus_c; }
@@ -238,10 +241,10 @@ template <typename Real, int DIM> struct NodeOut {
 template <typename Real, int DIM, int STRAT>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
                                           const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
-                                          const Real (&x)[DIM], Real tau, uint64_t id, uint32_t tree, uint32_t point,
-                                          NodeOut<Real, DIM> &o) {
+                                          const Real (&x)[DIM], Real tau, uint32_t id_lo, uint32_t id_hi,
+                                          uint32_t tree, uint32_t point, NodeOut<Real, DIM> &o) {
   using M = Math<Real>;
-  const uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree, point), p.rk0, p.rk1);
+  const uint4 w = philox4x32_10(make_uint4(id_lo, id_hi, tree, point), p.rk0, p.rk1);
   // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
   using F = Node<Real>;
   Real n[DIM];
@@ -253,8 +256,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     if (DIM > 1) n[DIM > 1 ? 1 : 0] = r * s;
   }
   if (DIM == 3) {
-    const uint4 w2 = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), tree | 0x80000000u, point),
-                                   p.rk0, p.rk1);
+    const uint4 w2 = philox4x32_10(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), p.rk0, p.rk1);
     const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w2.x)));
     n[DIM - 1] = r * F::cos2pi(uniform01<Real>(w2.y));
   }
@@ -282,7 +284,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   if (leaf) {
     const Real g = initial_data<Real, DIM>(p, base, o.y);
     if (STRAT == kStratB) {
-      o.factor = (Real)p.leaf_factor * g;
+      o.factor = Scalars<Real>::leaf(p) * g;
     } else {
       const Real lmc = Scalars<Real>::lam_minus_c(p);
       o.factor = (lmc == Real(0)) ? g : F::exp_scaled(lmc * tau) * g;

@@ -81,16 +81,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
   uint32_t tree = 0, point = 0;
   uint64_t rec = 0;
   Real base[DIM];
-  // lane: the current node and the running tree
+  // lane: the current node (position, remaining time, label) and the running tree
   Real x[DIM], tau = Real(0), W = Real(1);
-  uint64_t id = 0;
+  uint32_t id_lo = 0, id_hi = 0;
   int Ne = 0, depth = 0;
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     base[i] = Real(0);
     x[i] = Real(0);
   }
-  unsigned long long nodes = 0;
+  uint32_t nodes = 0;  // nodes this lane visited
 
   for (;;) {
     // ---- hand unstarted trees to idle lanes ---------------------------------
@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
         }
         tau = c_t;
         W = Real(1);
-        id = 0;
+        id_lo = 0;
+        id_hi = 0;
         Ne = 0;
         depth = 0;
         active = true;
@@ -141,63 +142,58 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
     if (!active) continue;
 
     // ---- one node -----------------------------------------------------------
+    // Straight-line form: the next node is the first child (down), the next
+    // pending sibling from the stack (up), or the tree is done.
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, id, tree, point, o);
+    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, id_lo, id_hi, tree, point, o);
     W *= o.factor;
-    bool done = false, pruned = false, descend = false;
-    if (o.cat >= 0) {
-      ++Ne;
-      if (Ne > K) {
-        pruned = true;
-        done = true;
-      } else {
-        const int k = s_arity[o.cat];
-        if (k > 0) {
-          if (k > 1) {  // remember the remaining children 2 .. k
-            const int at = depth * 32 + lane;
+    const bool split = o.cat >= 0;
+    Ne += split ? 1 : 0;
+    const bool pruned = Ne > K;  // can only become true at a split
+    const int k = (split && !pruned) ? s_arity[o.cat] : 0;
+    const bool down = k > 0;
+    if (k > 1) {  // remember the remaining children 2 .. k: labels 16 id + 2 .. 16 id + k
+      const int at = depth * 32 + lane;
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
-            stk_tau[at] = o.tau_c;
-            const uint64_t child0 = id * 16u;  // children of id are child0 + 1 .. child0 + k
-            stk_lo[at] = (uint32_t)child0;
-            stk_hi[at] = (uint32_t)(child0 >> 32);
-            stk_nk[at] = ((uint32_t)k << 8) | 2u;
-            ++depth;
-          }
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) x[i] = o.y[i];
-          tau = o.tau_c;
-          id = id * 16u + 1u;
-          descend = true;
-        }
-      }
+      for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
+      stk_tau[at] = o.tau_c;
+      stk_lo[at] = id_lo << 4;
+      stk_hi[at] = __funnelshift_l(id_lo, id_hi, 4);
+      stk_nk[at] = ((uint32_t)k << 8) | 2u;
+      ++depth;
     }
-    if (!descend && !done) {  // leaf (or arity-0 split): continue with the next pending sibling
-      if (depth == 0) {
-        done = true;
-      } else {
-        const int at = (depth - 1) * 32 + lane;
+    const bool up = !down && !pruned && depth > 0;
+    if (down) {  // first child: label 16 id + 1
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
-        tau = stk_tau[at];
-        const uint32_t nk = stk_nk[at];
-        const uint32_t nd = nk & 0xFFu;
-        id = (((uint64_t)stk_hi[at] << 32) | stk_lo[at]) + nd;
-        if (nd == (nk >> 8)) --depth;
-        else stk_nk[at] = nk + 1u;
-      }
+      for (int i = 0; i < DIM; ++i) x[i] = o.y[i];
+      tau = o.tau_c;
+      id_hi = __funnelshift_l(id_lo, id_hi, 4);
+      id_lo = (id_lo << 4) | 1u;
     }
-    if (done) {
+    if (up) {
+      const int at = (depth - 1) * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
+      tau = stk_tau[at];
+      const uint32_t nk = stk_nk[at];
+      const uint32_t nd = nk & 0xFFu;
+      id_lo = stk_lo[at] | nd;
+      id_hi = stk_hi[at];
+      if (nd == (nk >> 8)) --depth;
+      else stk_nk[at] = nk + 1u;
+    }
+    if (!down && !up) {  // leaf with nothing pending, or pruned
       reinterpret_cast<Real *>(p.rec_w)[rec] = pruned ? Real(0) : W;
       p.rec_o[rec] = (uint8_t)(pruned ? K + 1 : Ne);
       active = false;
     }
   }
   // nodes visited by this warp
+  unsigned long long tot = nodes;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(kFull, nodes, off);
-  if (lane == 0) atomicAdd(p.stats, nodes);
+  for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(kFull, tot, off);
+  if (lane == 0) atomicAdd(p.stats, tot);
 }
 
 // One thread per tree: per-tree records (diagnostic form of the same streams).
@@ -234,7 +230,7 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
   for (;;) {
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, id, tree, point, o);
+    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, (uint32_t)id, (uint32_t)(id >> 32), tree, point, o);
     h = (h ^ (uint64_t)(o.cat + 1)) * 0x100000001B3ull;
     W *= o.factor;
     bool descend = false;
