@@ -95,51 +95,61 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
   for (;;) {
     // ---- hand unstarted trees to idle lanes ---------------------------------
     unsigned idle = __ballot_sync(kFull, !active);
-    while (idle != 0u && !exhausted) {
-      if (c_next >= c_end) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(p.counter, 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= p.total_items) {
-          exhausted = true;
-          break;
-        }
-        const int pt = find_point(p.prefix, p.n, item, lane);
-        const uint32_t N = __ldg(p.ntrees + pt);
-        c_next = (item - __ldg(p.prefix + pt)) * (uint32_t)kTile;
-        c_end = min(c_next + (uint32_t)kTile, N);
-        c_point = p.point_base + (uint32_t)pt;
-        c_rec = __ldg(p.tree_prefix + pt);
-        c_t = (Real)__ldg(p.t + pt);
-        double xp[DIM];
+    if (idle != 0u) {
+      while (idle != 0u && !exhausted) {
+        if (c_next >= c_end) {
+          uint32_t item = 0;
+          if (lane == 0) item = atomicAdd(p.counter, 1u);
+          item = __shfl_sync(kFull, item, 0);
+          if (item >= p.total_items) {
+            exhausted = true;
+            break;
+          }
+          const int pt = find_point(p.prefix, p.n, item, lane);
+          const uint32_t N = __ldg(p.ntrees + pt);
+          c_next = (item - __ldg(p.prefix + pt)) * (uint32_t)kTile;
+          c_end = min(c_next + (uint32_t)kTile, N);
+          c_point = p.point_base + (uint32_t)pt;
+          c_rec = __ldg(p.tree_prefix + pt);
+          c_t = (Real)__ldg(p.t + pt);
+          double xp[DIM];
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) xp[i] = __ldg(p.x + (size_t)pt * DIM + i);
-        initial_data_base<Real, DIM>(p, xp, c_base);
-      }
-      const uint32_t avail = c_end - c_next;
-      const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
-      if (((idle >> lane) & 1u) && rank < avail) {
-        tree = c_next + rank;
-        point = c_point;
-        rec = c_rec + tree;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          base[i] = c_base[i];
-          x[i] = Real(0);
+          for (int i = 0; i < DIM; ++i) xp[i] = __ldg(p.x + (size_t)pt * DIM + i);
+          initial_data_base<Real, DIM>(p, xp, c_base);
         }
-        tau = c_t;
-        W = Real(1);
-        id_lo = 0;
-        id_hi = 0;
-        Ne = 0;
-        depth = 0;
-        active = true;
+        const uint32_t avail = c_end - c_next;
+        const uint32_t want = (uint32_t)__popc(idle);
+        const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
+        if (((idle >> lane) & 1u) && rank < avail) {
+          tree = c_next + rank;
+          point = c_point;
+          rec = c_rec + tree;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            base[i] = c_base[i];
+            x[i] = Real(0);
+          }
+          tau = c_t;
+          W = Real(1);
+          id_lo = 0;
+          id_hi = 0;
+          Ne = 0;
+          depth = 0;
+          active = true;
+        }
+        if (avail >= want) {  // every idle lane got a tree
+          c_next += want;
+          idle = 0u;
+        } else {
+          c_next = c_end;
+          idle = __ballot_sync(kFull, !active);
+        }
       }
-      c_next += min((uint32_t)__popc(idle), avail);
-      idle = __ballot_sync(kFull, !active);
+      if (exhausted) {  // the queue is empty: finish the trees in flight
+        if (!__any_sync(kFull, active)) break;
+        if (!active) continue;
+      }
     }
-    if (!__any_sync(kFull, active)) break;
-    if (!active) continue;
 
     // ---- one node -----------------------------------------------------------
     // Straight-line form: the next node is the first child (down), the next
