@@ -286,11 +286,12 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   std::vector<uint32_t> prefix((size_t)n + 1), nt32((size_t)n);
   std::vector<unsigned long long> tprefix((size_t)n + 1);
   std::vector<uint32_t> cprefix((size_t)n + 1);
-  uint64_t items = 0, trees = 0, chunks = 0;
+  uint64_t items = 0, trees = 0, chunks = 0, recs = 0;  // recs: record slots, each point's segment 4-aligned
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
     prefix[(size_t)i] = (uint32_t)items;
-    tprefix[(size_t)i] = trees;
+    tprefix[(size_t)i] = recs;
+    recs += (ntrees[i] + 3) & ~(uint64_t)3;
     cprefix[(size_t)i] = (uint32_t)chunks;
     chunks += ntrees[i] == 0 ? 1 : (ntrees[i] + grt::kBinChunk - 1) / grt::kBinChunk;
     items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
@@ -299,15 +300,15 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
     if (items >= 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "too many work items (total trees too large)");
   }
   prefix[(size_t)n] = (uint32_t)items;
-  tprefix[(size_t)n] = trees;
+  tprefix[(size_t)n] = recs;
   cprefix[(size_t)n] = (uint32_t)chunks;
   if (chunks > 0x7FFFFFFFull) return c->set_error(GRT_EINVAL, "too many binning chunks (total trees too large)");
   GRT_CUDA(c, cudaSetDevice(c->device));
   GRT_CUDA(c, p->prefix.ensure(prefix.size() * sizeof(uint32_t)));
   GRT_CUDA(c, p->tree_prefix.ensure(tprefix.size() * sizeof(unsigned long long)));
   GRT_CUDA(c, p->ntrees.ensure(nt32.size() * sizeof(uint32_t) + 4));
-  GRT_CUDA(c, p->rec_w.ensure((size_t)trees * acc_size(c) + 16));
-  GRT_CUDA(c, p->rec_o.ensure((size_t)trees + 16));
+  GRT_CUDA(c, p->rec_w.ensure((size_t)recs * acc_size(c) + 64));
+  GRT_CUDA(c, p->rec_o.ensure((size_t)recs + 64));
   GRT_CUDA(c, p->chunk_prefix.ensure(cprefix.size() * sizeof(uint32_t)));
   GRT_CUDA(c, p->part.ensure((size_t)chunks * 4 * (K + 2) * sizeof(double) + 16));
   p->work_bytes = 64 + (((size_t)n * sizeof(uint32_t) + 63) & ~(size_t)63);
@@ -677,8 +678,9 @@ constexpr size_t kNaTreePrefix = na_align(kNaPrefix + (GRT_NOALLOC_MAX_POINTS + 
 constexpr size_t kNaNtrees = na_align(kNaTreePrefix + (GRT_NOALLOC_MAX_POINTS + 1) * sizeof(unsigned long long));
 constexpr size_t kNaChunkPrefix = na_align(kNaNtrees + GRT_NOALLOC_MAX_POINTS * sizeof(uint32_t));
 constexpr size_t kNaRecO = na_align(kNaChunkPrefix + (GRT_NOALLOC_MAX_POINTS + 1) * sizeof(uint32_t));
-constexpr size_t kNaRecW = na_align(kNaRecO + GRT_NOALLOC_MAX_TREES);
-constexpr size_t kNaPart = na_align(kNaRecW + (size_t)GRT_NOALLOC_MAX_TREES * sizeof(double));
+constexpr size_t kNaRecSlots = (size_t)GRT_NOALLOC_MAX_TREES + 4 * (size_t)GRT_NOALLOC_MAX_POINTS;  // 4-aligned
+constexpr size_t kNaRecW = na_align(kNaRecO + kNaRecSlots);
+constexpr size_t kNaPart = na_align(kNaRecW + kNaRecSlots * sizeof(double));
 constexpr size_t kNaBytes = na_align(kNaPart + kNoAllocMaxChunks * 4 * (GRT_MAX_K + 2) * sizeof(double));
 
 // The library's fixed work area (about 7 MB).  Host code must not use this
@@ -722,11 +724,12 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
   // work layout on the host, in fixed-size arrays on this thread's stack (no heap)
   uint32_t prefix[GRT_NOALLOC_MAX_POINTS + 1], nt32[GRT_NOALLOC_MAX_POINTS], cprefix[GRT_NOALLOC_MAX_POINTS + 1];
   unsigned long long tprefix[GRT_NOALLOC_MAX_POINTS + 1];
-  uint64_t items = 0, trees = 0, chunks = 0;
+  uint64_t items = 0, trees = 0, chunks = 0, recs = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
     prefix[i] = (uint32_t)items;
-    tprefix[i] = trees;
+    tprefix[i] = recs;
+    recs += (ntrees[i] + 3) & ~(uint64_t)3;
     cprefix[i] = (uint32_t)chunks;
     nt32[i] = (uint32_t)ntrees[i];
     items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
@@ -736,7 +739,7 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
       return c->set_error(GRT_EINVAL, "grt_solve_noalloc: total trees above GRT_NOALLOC_MAX_TREES (524288)");
   }
   prefix[n] = (uint32_t)items;
-  tprefix[n] = trees;
+  tprefix[n] = recs;
   cprefix[n] = (uint32_t)chunks;
 
   GRT_CUDA(c, cudaSetDevice(c->device));

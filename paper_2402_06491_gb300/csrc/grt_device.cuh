@@ -50,7 +50,7 @@ struct WalkParams {
   const double *t;           // [n]
   const uint32_t *ntrees;    // [n]
   const uint32_t *prefix;    // [n+1] first queue chunk of each point
-  const unsigned long long *tree_prefix;  // [n+1] first record of each point
+  const unsigned long long *tree_prefix;  // [n+1] first record slot of each point (4-aligned segments)
   int n;
   uint32_t total_items;      // queue chunks
   void *rec_w;               // [total trees] tree weights (float or double)

@@ -21,6 +21,29 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double v) {
   s = t;
 }
 
+// Per-order accumulator slot of one binning thread, one 16-byte (float) or
+// 32-byte (double) shared-memory access per record.
+template <typename Acc> struct alignas(4 * sizeof(Acc)) Acc4 {
+  Acc s1, c1, s2, sa;
+};
+
+// Four consecutive tree weights (16-byte aligned for float, 32 for double).
+__device__ __forceinline__ void load4(const float *p, float (&w)[4]) {
+  const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+  w[0] = v.x;
+  w[1] = v.y;
+  w[2] = v.z;
+  w[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&w)[4]) {
+  const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+  w[0] = a.x;
+  w[1] = a.y;
+  w[2] = b.x;
+  w[3] = b.y;
+}
+
 // [L/M] Pade of sum a_n eps^n at eps = 1.  The series is first rescaled,
 // c_n = a_n / rho^n with rho = 2^k, k = max_{j > m} ceil((e_j - e_m)/(j - m)),
 // e_j the binary exponent of a_j and m the first nonzero term: this leaves the
@@ -124,9 +147,9 @@ __device__ double pade_value(const double *a, int L, int M, int *status) {
 
 // Binning (Sec. 2.4: trees of order n give the n-th series coefficient).
 // One block per chunk of kBinChunk consecutive tree records of one point.
-// Thread j bins records j, j + T, j + 2T, ... of the chunk (T = kFinThreads)
-// into its own shared-memory column of per-order sums (S1 with Kahan
-// compensation, S2, S|W|, count); the columns are added in a fixed order and
+// Thread j bins record groups 4j .. 4j+3, 4(j+T) .. 4(j+T)+3, ... of the chunk
+// (T = kFinThreads) into its own shared-memory column of per-order sums (S1
+// with Kahan compensation, S2, S|W|, count); the columns are added in a fixed order and
 // the chunk's sums written to `part`.  The last block to finish a point
 // (fence + ticket, nobody waits) adds the point's chunk sums in chunk order,
 // forms a_n and SE_n and runs the FP64 Pade.  Every result depends only on
@@ -149,59 +172,60 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
     }
     s_pt = lo;
   }
-  Acc *s1 = reinterpret_cast<Acc *>(smem);  // [R][T] each
-  Acc *c1 = s1 + R * T;
-  Acc *s2 = c1 + R * T;
-  Acc *sa = s2 + R * T;
-  uint32_t *cn = reinterpret_cast<uint32_t *>(sa + R * T);
+  // per-thread columns: acc[o * T + tid] = (S1, Kahan compensation of S1, S2, S|W|), cn = count
+  Acc4<Acc> *acc = reinterpret_cast<Acc4<Acc> *>(smem);
+  uint32_t *cn = reinterpret_cast<uint32_t *>(acc + R * T);
   for (int r = 0; r < R; ++r) {
-    s1[r * T + tid] = Acc(0);
-    c1[r * T + tid] = Acc(0);
-    s2[r * T + tid] = Acc(0);
-    sa[r * T + tid] = Acc(0);
+    acc[r * T + tid] = Acc4<Acc>{Acc(0), Acc(0), Acc(0), Acc(0)};
     cn[r * T + tid] = 0u;
   }
   __syncthreads();
   const int pt = s_pt;
-  const unsigned long long r0 = f.tree_prefix[pt] + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
-  const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, f.tree_prefix[pt + 1]);
+  // this chunk's records [r0, r1); r0 is a multiple of 4 (4-aligned point segments, 8192-record chunks)
+  const unsigned long long seg = f.tree_prefix[pt];
+  const unsigned long long r0 = seg + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
+  const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, seg + f.ntrees[pt]);
   const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
-  constexpr int BATCH = 8;  // records per thread per batch; the next batch is in flight meanwhile
-  constexpr int STEP = BATCH * T;
-  int oa[BATCH], ob[BATCH];
-  Acc wa[BATCH], wb[BATCH];
-  auto load = [&](int (&ord)[BATCH], Acc (&wv)[BATCH], int b0) {
+  auto bin = [&](uint32_t o4, const Acc (&w4)[4], unsigned long long i) {
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
-      const unsigned long long i = r0 + (unsigned long long)(b0 + j * T + tid);
-      const bool in = b0 < kBinChunk && i < r1;
-      ord[j] = in ? (int)__ldcs(f.rec_o + i) : -1;
-      wv[j] = in ? __ldcs(rw + i) : Acc(0);
-    }
-  };
-  auto bin = [&](const int (&ord)[BATCH], const Acc (&wv)[BATCH]) {
-#pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
-      const int o = ord[j];
-      if (o < 0) continue;
-      const Acc w = wv[j];
+    for (int q = 0; q < 4; ++q) {
+      if (i + q >= r1) break;
+      const int o = (int)((o4 >> (8 * q)) & 0xFFu);
       const int a = o * T + tid;
       if (o <= K) {
-        kahan_add(s1[a], c1[a], w);
-        s2[a] += w * w;
-        sa[a] += w < Acc(0) ? -w : w;
+        const Acc w = w4[q];
+        Acc4<Acc> v = acc[a];
+        kahan_add(v.s1, v.c1, w);
+        v.s2 += w * w;
+        v.sa += w < Acc(0) ? -w : w;
+        acc[a] = v;
       }
       cn[a] += 1u;
     }
   };
-  const int span = (int)min((unsigned long long)kBinChunk, r1 - r0);  // records of this chunk
-  load(oa, wa, 0);
+  // thread tid takes record groups r0 + 4 (tid + j T): one 32-bit load of four orders and one
+  // vector load of four weights per group, the next group in flight while this one is binned
+  unsigned long long i = r0 + 4ull * tid;
+  uint32_t oa = 0;
+  Acc wa[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+  if (i < r1) {
+    oa = __ldcs(reinterpret_cast<const uint32_t *>(f.rec_o + i));
+    load4(rw + i, wa);
+  }
 #pragma unroll 1
-  for (int b0 = 0; b0 < span; b0 += 2 * STEP) {
-    load(ob, wb, b0 + STEP);
-    bin(oa, wa);
-    load(oa, wa, b0 + 2 * STEP);
-    bin(ob, wb);
+  while (i < r1) {
+    const unsigned long long in = i + 4ull * T;
+    uint32_t ob = 0;
+    Acc wb[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    if (in < r1) {
+      ob = __ldcs(reinterpret_cast<const uint32_t *>(f.rec_o + in));
+      load4(rw + in, wb);
+    }
+    bin(oa, wa, i);
+    i = in;
+    oa = ob;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wa[q] = wb[q];
   }
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
@@ -211,9 +235,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
     Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
     uint32_t ac = 0;
     for (int j = lane; j < T; j += 32) {
-      kahan_add(a1, k1, s1[r * T + j] - c1[r * T + j]);
-      kahan_add(a2, k2, s2[r * T + j]);
-      kahan_add(a3, k3, sa[r * T + j]);
+      const Acc4<Acc> v = acc[r * T + j];
+      kahan_add(a1, k1, v.s1 - v.c1);
+      kahan_add(a2, k2, v.s2);
+      kahan_add(a3, k3, v.sa);
       ac += cn[r * T + j];
     }
     // butterfly in the walk's precision (FP64 arithmetic is scarce on this GPU:
@@ -289,7 +314,7 @@ __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, doub
 }
 
 template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParams &f, cudaStream_t stream) {
-  const size_t smem = (size_t)(f.K + 2) * kFinThreads * (4 * sizeof(Acc) + sizeof(uint32_t));
+  const size_t smem = (size_t)(f.K + 2) * kFinThreads * (sizeof(Acc4<Acc>) + sizeof(uint32_t));
   cudaError_t e = cudaFuncSetAttribute(finalize_kernel<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   finalize_kernel<Acc><<<f.total_chunks, kFinThreads, smem, stream>>>(f);

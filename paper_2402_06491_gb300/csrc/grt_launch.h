@@ -13,7 +13,7 @@ struct WalkParams;
 struct FinalizeParams {
   const void *rec_w;         // [total trees] tree weights (float or double)
   const uint8_t *rec_o;      // [total trees] tree orders (K+1 = pruned)
-  const unsigned long long *tree_prefix;  // [n+1]
+  const unsigned long long *tree_prefix;  // [n+1] first record slot of each point (multiples of 4)
   const uint32_t *ntrees;    // [n]
   const uint32_t *chunk_prefix;  // [n+1] first binning chunk of each point (every point has >= 1)
   uint32_t total_chunks;
