@@ -14,36 +14,14 @@
 #include <vector>
 
 #include "grt_device.cuh"
+#include "grt_host.h"
 #include "grt_launch.h"
 
 namespace {
 
 thread_local std::string g_create_error;
 
-struct DevBuf {
-  void *ptr = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap && ptr) return cudaSuccess;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    cap = 0;
-    size_t want = bytes < 256 ? 256 : bytes;
-    cudaError_t e = cudaMalloc(&ptr, want);
-    if (e != cudaSuccess) {
-      ptr = nullptr;
-      return e;
-    }
-    cap = want;
-    return cudaSuccess;
-  }
-  void release() {
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    cap = 0;
-  }
-  template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
-};
+
 
 // Threshold of a cumulative probability on the 32-bit word scale:
 // round-to-nearest of 2^32 * cum, clamped to [0, 2^32].
@@ -58,27 +36,6 @@ bool is_finite(double v) { return std::isfinite(v); }
 
 }  // namespace
 
-struct grt_plan;
-
-struct grt_ctx {
-  grt_problem pb{};
-  int device = 0;
-  int num_sms = 0;
-  grt::WalkParams base{};
-  std::string err;
-  cudaStream_t stream = nullptr;
-  grt_plan *solve_plan = nullptr;
-  DevBuf dx, dt, du, dcoef, dse, dstatus;
-  int set_error(int code, const std::string &msg) {
-    err = msg;
-    return code;
-  }
-  int cuda_error(cudaError_t e, const char *where) {
-    err = std::string(where) + ": " + cudaGetErrorString(e);
-    return GRT_EDEVICE;
-  }
-};
-
 struct grt_plan {
   grt_ctx *ctx = nullptr;
   int64_t n = 0;
@@ -87,8 +44,8 @@ struct grt_plan {
   uint64_t total_trees = 0;
   std::vector<uint64_t> host_ntrees;
   uint32_t total_chunks = 0;
-  DevBuf prefix, tree_prefix, ntrees, rec_w, rec_o, chunk_prefix, part;
-  DevBuf work;  // queue head (8 B), 3 u64 counters, then n u32 chunk tickets
+  grt::DevBuf prefix, tree_prefix, ntrees, rec_w, rec_o, chunk_prefix, part;
+  grt::DevBuf work;  // queue head (8 B), 3 u64 counters, then n u32 chunk tickets
   size_t work_bytes = 64;
   cudaStream_t last_stream = nullptr;
   int launches = 0;
@@ -113,11 +70,7 @@ struct grt_plan {
 
 namespace {
 
-#define GRT_CUDA(ctx, expr)                                        \
-  do {                                                             \
-    cudaError_t e_ = (expr);                                       \
-    if (e_ != cudaSuccess) return (ctx)->cuda_error(e_, #expr);    \
-  } while (0)
+
 
 // Validate the problem and build the walk's tables (branching law of
 // Sec. 2.1 Eq. probexp2 / Sec. 2.2 Eq. probexpB1 on 32-bit thresholds).
@@ -580,7 +533,7 @@ int grt_pade(grt_ctx *c, int64_t n, int K, int L, int M, const double *coef, dou
   if (n == 0) return GRT_OK;
   if (!coef || !u_out) return c->set_error(GRT_EINVAL, "coef and u_out must be non-NULL");
   GRT_CUDA(c, cudaSetDevice(c->device));
-  DevBuf dc, du, ds;
+  grt::DevBuf dc, du, ds;
   auto cleanup = [&]() {
     dc.release();
     du.release();
@@ -622,7 +575,7 @@ int grt_trees(grt_ctx *c, const double *x, double t, uint64_t point_index, uint6
   p.K = K;
   double x0[3] = {0, 0, 0};
   for (int d = 0; d < c->pb.dim; ++d) x0[d] = x[d];
-  DevBuf bo, bw, bn, bh;
+  grt::DevBuf bo, bw, bn, bh;
   auto cleanup = [&]() {
     bo.release();
     bw.release();

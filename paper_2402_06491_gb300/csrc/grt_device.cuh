@@ -51,6 +51,8 @@ struct WalkParams {
   const uint32_t *ntrees;    // [n]
   const uint32_t *prefix;    // [n+1] first queue chunk of each point
   const unsigned long long *tree_prefix;  // [n+1] first record slot of each point (4-aligned segments)
+  const uint32_t *tree_first;  // [n] first tree index walked for each point, or null (0): incremental solves
+  const uint32_t *point_id;    // [n] random-stream point index of each point, or null (point_base + p)
   int n;
   uint32_t total_items;      // queue chunks
   void *rec_w;               // [total trees] tree weights (float or double)

@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
   // columns l, l+32, ... with compensation, then a fixed butterfly over lanes
-  double *part = f.part + (size_t)chunk * 4 * R;
+  const size_t pstride = f.part_stride ? f.part_stride : (size_t)4 * R;
+  const uint32_t cfirst = f.tree_first ? f.tree_first[pt] : 0u;
+  const uint32_t slot0 = f.part_slot ? f.part_slot[pt] : f.chunk_prefix[pt];
+  double *part = f.part + (size_t)(slot0 + cfirst / kBinChunk + (chunk - f.chunk_prefix[pt])) * pstride;
   for (int r = warp; r < R; r += T / 32) {
     Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
     uint32_t ac = 0;
@@ -267,24 +270,29 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   }
   __syncthreads();
   if (!s_last) return;
+  // this launch has all its chunks of the point; is the point complete?
+  const uint32_t ntot = f.ntotal ? f.ntotal[pt] : f.ntrees[pt];
+  if (cfirst + f.ntrees[pt] != ntot) return;  // more trees in a later launch: partials stay resident
   __threadfence();
   __shared__ double tot[4][kMaxK + 2];
   __shared__ double a[kMaxK + 1];
   if (tid < 4 * R) {  // thread (stat, row) adds the point's chunk sums in chunk order
-    const double *pp = f.part + (size_t)f.chunk_prefix[pt] * 4 * R + tid;
-    const uint32_t nch = f.chunk_prefix[pt + 1] - f.chunk_prefix[pt];
+    const double *pp = f.part + (size_t)slot0 * pstride + tid;
+    const uint32_t nch = ntot == 0u ? 1u : (ntot + kBinChunk - 1) / kBinChunk;
     double s = 0.0, c = 0.0;
-    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * 4 * R));
+    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
     tot[tid / R][tid % R] = s - c;
   }
   __syncthreads();
-  const double N = (double)f.ntrees[pt];
+  const double N = (double)ntot;
+  const size_t row = f.out_slot ? f.out_slot[pt] : (size_t)pt;
+  const size_t ostride = f.out_stride ? f.out_stride : (size_t)(K + 1);
   if (tid <= K) {
     const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
     const double var = N > 1.0 ? (tot[1][tid] / N - an * an) / (N - 1.0) : 0.0;
     a[tid] = an;
-    if (f.coef) f.coef[(size_t)pt * (K + 1) + tid] = an;
-    if (f.se) f.se[(size_t)pt * (K + 1) + tid] = var > 0.0 ? sqrt(var) : 0.0;
+    if (f.coef) f.coef[row * ostride + tid] = an;
+    if (f.se) f.se[row * ostride + tid] = var > 0.0 ? sqrt(var) : 0.0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -294,8 +302,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
     int st = 0;
     const double u = pade_value(a, f.L, f.M, &st);
     if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
-    f.u[pt] = u;
-    if (f.status) f.status[pt] = st;
+    f.u[row] = u;
+    if (f.status) f.status[row] = st;
     if (f.stats) {
       atomicAdd(f.stats + 1, (unsigned long long)splits);
       atomicAdd(f.stats + 2, (unsigned long long)pruned);

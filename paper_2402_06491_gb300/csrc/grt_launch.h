@@ -15,10 +15,17 @@ struct FinalizeParams {
   const uint8_t *rec_o;      // [total trees] tree orders (K+1 = pruned)
   const unsigned long long *tree_prefix;  // [n+1] first record slot of each point (multiples of 4)
   const uint32_t *ntrees;    // [n]
-  const uint32_t *chunk_prefix;  // [n+1] first binning chunk of each point (every point has >= 1)
+  const uint32_t *chunk_prefix;  // [n+1] first binning chunk of each point in this launch (every point has >= 1)
   uint32_t total_chunks;
-  double *part;              // [chunks][4][K+2] per-chunk sums: S1, S2, S|W|, count
+  double *part;              // per-chunk sums S1, S2, S|W|, count: [slot][4][K+2], slot stride part_stride
   uint32_t *done;            // [n] chunks of each point finished (zeroed before the launch)
+  // incremental solves (all null for a one-shot solve):
+  const uint32_t *tree_first;  // [n] first tree of this launch's range (a multiple of kBinChunk), null: 0
+  const uint32_t *ntotal;      // [n] the point's whole budget, null: ntrees (the point completes here)
+  const uint32_t *part_slot;   // [n] first chunk slot of the point in `part`, null: chunk_prefix[p]
+  const uint32_t *out_slot;    // [n] output row of the point, null: p
+  size_t part_stride;          // doubles between chunk slots, 0: 4 (K+2)
+  size_t out_stride;           // doubles between coef / se rows, 0: K+1
   int n, K, L, M;
   double *u;                 // [n]
   double *coef, *se;         // [n][K+1] or null

@@ -11,7 +11,9 @@
 // and no lane idles at chunk boundaries.
 //
 // Each finished tree writes its record (order Ne or K+1 if pruned, weight W)
-// to its slot in HBM: rec_o / rec_w [tree_prefix[p] + tree].  The series
+// to its slot in HBM: rec_o / rec_w [tree_prefix[p] + tree - tree_first[p]].
+// (An incremental solve walks trees tree_first[p] .. tree_first[p] + ntrees[p] - 1
+// of point p; a one-shot solve has tree_first = 0.)  The series
 // binning of Sec. 2.4 is done from these records by the finalize kernel in a
 // fixed order, so results do not depend on which lane walked which tree.
 #include "grt_device.cuh"
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
   const unsigned lt_mask = (1u << lane) - 1u;
 
   // warp-uniform: the chunk trees are handed out from
-  uint32_t c_next = 0, c_end = 0, c_point = 0;
+  uint32_t c_next = 0, c_end = 0, c_point = 0, c_first = 0;
   uint64_t c_rec = 0;
   Real c_t = Real(0), c_base[DIM];
 #pragma unroll
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
           const uint32_t N = __ldg(p.ntrees + pt);
           c_next = (item - __ldg(p.prefix + pt)) * (uint32_t)kTile;
           c_end = min(c_next + (uint32_t)kTile, N);
-          c_point = p.point_base + (uint32_t)pt;
+          c_point = p.point_id ? __ldg(p.point_id + pt) : p.point_base + (uint32_t)pt;
+          c_first = p.tree_first ? __ldg(p.tree_first + pt) : 0u;
           c_rec = __ldg(p.tree_prefix + pt);
           c_t = (Real)__ldg(p.t + pt);
           double xp[DIM];
@@ -121,9 +124,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
         const uint32_t want = (uint32_t)__popc(idle);
         const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
         if (((idle >> lane) & 1u) && rank < avail) {
-          tree = c_next + rank;
+          tree = c_first + c_next + rank;  // the tree's index in its point's stream
           point = c_point;
-          rec = c_rec + tree;
+          rec = c_rec + c_next + rank;
 #pragma unroll
           for (int i = 0; i < DIM; ++i) {
             base[i] = c_base[i];
