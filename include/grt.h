@@ -56,6 +56,7 @@ extern "C" {
 #define GRT_EDEVICE (-3)  /* a CUDA call failed (no device, launch error...) */
 #define GRT_ETIMEOUT (-4) /* a bounded device wait ran out                   */
 #define GRT_ENOTSUP (-5)  /* valid request this build does not support       */
+#define GRT_EAGAIN 1      /* (grt_poll) the request has not finished yet      */
 
 /* Strategy (Sec. 2.1 / Sec. 2.2). */
 #define GRT_STRATEGY_A 0
@@ -185,6 +186,50 @@ int grt_pade(grt_ctx *ctx, int64_t n, int K, int L, int M, const double *coef, d
  * A diagnostic of the same streams the point solve uses (Sec. 2.2, Fig. 2). */
 int grt_trees(grt_ctx *ctx, const double *x, double t, uint64_t point_index, uint64_t first_tree, uint64_t ntrees,
               int K, uint64_t seed, int32_t *order, double *w, uint32_t *nodes, uint64_t *hash);
+
+/* ---- Serving: continuous batching of point-solve requests (the serving form
+ * of the probabilistic part of the PDD, Sec. 3). ----------------------------
+ * A server owns a scheduler thread and a device-memory budget on one device.
+ * Requests (a problem context, points, per-point tree budgets, K, L, M, seed)
+ * may be submitted at any time from any thread; each is admitted when its
+ * resident state (per-point chunk sums of 8192 trees, result rows) fits the
+ * budget, first come first admitted.  The scheduler runs the GPU in steps of at
+ * most `step_trees` trees taken from all admitted requests, smallest remaining
+ * work first, in ranges that start on a point's 8192-tree boundaries; requests
+ * of one problem, K, L, M and seed share one walk and one binning launch per
+ * step.  A point's result is identical, bit for bit, to grt_solve of the same
+ * point (same point_base + index and seed), alone or in any mix.
+ * Contexts passed to grt_submit must outlive their requests. */
+typedef struct grt_server grt_server;
+
+/* mem_budget_bytes: device memory for step buffers and resident state (at least
+ * step_trees x 9 bytes + 80 bytes per step point + 1 MB; step points =
+ * clamp(step_trees / 256, 4096, 2^20)); step_trees: trees per step (0: 2^27).
+ * GRT_EINVAL if the budget is too small, GRT_ENOMEM / GRT_EDEVICE on failure. */
+int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees, grt_server **out);
+
+/* Stop the scheduler (after its current step) and free the server and any
+ * requests not yet polled.  NULL is ignored. */
+void grt_server_destroy(grt_server *s);
+
+const char *grt_server_last_error(const grt_server *s);
+
+/* Copy a request's inputs (HOST arrays, grt_solve's layout) and queue it;
+ * returns at once with *request_id.  GRT_ENOMEM if the request alone exceeds
+ * the budget. */
+int grt_submit(grt_server *s, grt_ctx *ctx, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K,
+               int L, int M, uint64_t seed, uint64_t point_base, uint64_t *request_id);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: wait until done) for a request.
+ * Done: writes u_out [n], coef_out / se_out [n][K+1], status_out [n] (any may be
+ * NULL) and *latency_s (submit to completion), releases the request and returns
+ * GRT_OK (or the request's error).  Not done: GRT_EAGAIN. */
+int grt_poll(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
+             int32_t *status_out, double *latency_s);
+
+/* Steps run, trees walked, kernel launches, resident bytes, pending and active requests. */
+int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *launches, uint64_t *resident_bytes,
+                     uint64_t *pending_requests, uint64_t *active_requests);
 
 /* Limits of grt_solve_noalloc. */
 #define GRT_NOALLOC_MAX_POINTS 4096

@@ -19,7 +19,7 @@ MAX_DIM = 3
 MAX_DEG = 15
 MAX_K = 16
 
-OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP, EAGAIN = 0, -1, -2, -3, -4, -5, 1
 STRATEGY = {"A": 0, "B": 1}
 ARITY_LAW = {"uniform": 0, "abs": 1}
 PRECISION = {"fp32": 0, "fp64": 1}
@@ -79,6 +79,12 @@ def _load():
         "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
         "grt_solve_noalloc": ([_vp, i64, _vp, _vp, u64p, i32, i32, i32, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
+        "grt_server_create": ([i32, u64, u64, _P(_vp)], i32),
+        "grt_server_destroy": ([_vp], None),
+        "grt_server_last_error": ([_vp], ctypes.c_char_p),
+        "grt_submit": ([_vp, _vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, u64p], i32),
+        "grt_poll": ([_vp, u64, i32, f64p, f64p, f64p, i32p, f64p], i32),
+        "grt_server_stats": ([_vp, u64p, u64p, u64p, u64p, u64p, u64p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +198,11 @@ def _check(rc: int, ctx_handle=None):
     if rc != OK:
         msg = _load().grt_last_error(ctx_handle)
         raise GrtError(rc, msg.decode() if msg else "")
+
+
+def grt_server_last_error(server: Server) -> str:
+    msg = _load().grt_server_last_error(server.handle)
+    return msg.decode() if msg else ""
 
 
 def grt_last_error(ctx: Context | None) -> str:
@@ -342,6 +353,93 @@ def grt_solve_noalloc(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: 
     _check(rc, ctx.handle)
 
 
+class Server:
+    """A libgrt serving instance (grt_server): scheduler thread + device-memory budget."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self.requests = {}  # request id -> (n, K)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("server is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            _load().grt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_server(rc: int, server: "Server"):
+    if rc != OK:
+        msg = _load().grt_server_last_error(server._h)
+        raise GrtError(rc, msg.decode() if msg else "")
+
+
+def grt_server_create(device: int = 0, mem_budget_bytes: int = 2 << 30, step_trees: int = 0) -> Server:
+    h = _vp()
+    rc = _load().grt_server_create(int(device), int(mem_budget_bytes), int(step_trees), ctypes.byref(h))
+    if rc != OK:
+        raise GrtError(rc, "grt_server_create failed")
+    return Server(h.value)
+
+
+def grt_server_destroy(server: Server) -> None:
+    server.close()
+
+
+def grt_submit(server: Server, ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int,
+               point_base: int = 0) -> int:
+    """Queue a point-solve request (host arrays are copied); returns its id at once."""
+    lib = _load()
+    d = ctx.dim
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
+    n = xs.shape[0]
+    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
+    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    rid = ctypes.c_uint64(0)
+    _check_server(lib.grt_submit(server.handle, ctx.handle, n, _ptr(xs, ctypes.c_double), _ptr(ts, ctypes.c_double),
+                                 _ptr(nt, ctypes.c_uint64), K, L, M, int(seed), int(point_base),
+                                 ctypes.byref(rid)), server)
+    server.requests[rid.value] = (n, K)
+    return rid.value
+
+
+def grt_poll(server: Server, request_id: int, timeout_ms: int = -1):
+    """Results of a request (dict with u, coef, se, status, latency_s), or None if not finished."""
+    lib = _load()
+    n, K = server.requests[request_id]
+    u = np.empty(n, np.float64)
+    coef = np.empty((n, K + 1), np.float64)
+    se = np.empty((n, K + 1), np.float64)
+    st = np.empty(n, np.int32)
+    lat = ctypes.c_double(0)
+    rc = lib.grt_poll(server.handle, int(request_id), int(timeout_ms), _ptr(u, ctypes.c_double),
+                      _ptr(coef, ctypes.c_double), _ptr(se, ctypes.c_double), _ptr(st, ctypes.c_int32),
+                      ctypes.byref(lat))
+    if rc == EAGAIN:
+        return None
+    del server.requests[request_id]
+    _check_server(rc, server)
+    return dict(u=u, coef=coef, se=se, status=st, latency_s=lat.value)
+
+
+def grt_server_stats(server: Server) -> dict:
+    vals = [ctypes.c_uint64(0) for _ in range(6)]
+    _check_server(_load().grt_server_stats(server.handle, *[ctypes.byref(v) for v in vals]), server)
+    keys = ["steps", "trees", "launches", "resident_bytes", "pending", "active"]
+    return {k: int(v.value) for k, v in zip(keys, vals)}
+
+
 EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
-            "grt_pade", "grt_trees", "grt_solve_noalloc"]
+            "grt_pade", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
+            "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats"]
