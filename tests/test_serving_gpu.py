@@ -109,7 +109,8 @@ def test_errors_and_empty_requests(grt):
     ctx = grt.grt_create(wl["problem"], 0)
     with pytest.raises(grt.GrtError):
         grt.grt_server_create(0, mem_budget_bytes=1 << 20, step_trees=1 << 16)  # budget below the step buffers
-    server = grt.grt_server_create(0, mem_budget_bytes=256 << 20, step_trees=1 << 16)
+    # 64 MB: ~86K resident chunk rows; a point of 2^31 - 1 trees needs 262144
+    server = grt.grt_server_create(0, mem_budget_bytes=64 << 20, step_trees=1 << 16)
     rid = grt.grt_submit(server, ctx, np.zeros((0, 2)), np.zeros(0), np.zeros(0, np.uint64), 10, 5, 5, 0)
     r = grt.grt_poll(server, rid, 0)
     assert r is not None and r["u"].shape == (0,)
