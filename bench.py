@@ -250,6 +250,99 @@ def reference_arm(args) -> int:
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson trace through the continuous-batching server vs the plain path
+# ---------------------------------------------------------------------------
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, float), q)) if len(v) else None
+
+
+def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, plain_requests: int,
+                  plain_cap_s: float) -> dict:
+    probs = workloads.serving_problems("fp32")
+    ctxs = {k: grt.grt_create(v["problem"], dev) for k, v in probs.items()}
+    mean_trees = workloads.serving_mean_trees()
+    rate = 0.7 * capacity_trees_per_s / mean_trees
+    trace = workloads.serving_trace(n_requests, rate, seed=0)
+    server = grt.grt_server_create(dev, mem_budget_bytes=16 << 30, step_trees=1 << 26)
+    # warm-up: one small request per problem (first launch of every kernel instantiation)
+    warm = []
+    for k, v in probs.items():
+        d = v["problem"]["dim"]
+        warm.append(grt.grt_submit(server, ctxs[k], np.zeros((4, d)), np.full(4, 0.5), np.full(4, 20000, np.uint64),
+                                   v["K"], v["L"], v["M"], 99))
+    for rid in warm:
+        grt.grt_poll(server, rid, -1)
+    st0 = grt.grt_server_stats(server)
+    ids = [None] * len(trace)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, r in enumerate(trace):
+            delay = t0 + r["arrival"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            v = probs[r["key"]]
+            ids[k] = grt.grt_submit(server, ctxs[r["key"]], r["x"], r["t"], r["ntrees"], v["K"], v["L"], v["M"],
+                                    r["seed"], r["point_base"])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = [None] * len(trace)
+    for k in range(len(trace)):
+        while ids[k] is None:
+            time.sleep(0.0005)
+        res = grt.grt_poll(server, ids[k], -1)
+        lat[k] = res["latency_s"]
+    t_end = time.perf_counter()
+    th.join()
+    st1 = grt.grt_server_stats(server)
+    server.close()
+    points = int(sum(len(r["t"]) for r in trace))
+    trees = float(sum(float(r["ntrees"].sum()) for r in trace))
+    wall = t_end - t0
+    out = {
+        "trace": f"{len(trace)} Poisson requests at {rate:.1f} req/s (0.7 x the measured sin_2d capacity / mean "
+                 f"request of {mean_trees:.3g} trees); 1-4096 points log-uniform, 1e3-1e7 trees per point "
+                 f"log-uniform; f in (u^2-u, sin u, u-u^3) x d in (1, 2, 3); 16 GB admission budget; 2^26-tree steps",
+        "requests": len(trace), "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
+        "mean_ms": 1e3 * float(np.mean(lat)), "points_per_s": points / wall, "trees_per_s": trees / wall,
+        "wall_s": wall, "steps": st1["steps"] - st0["steps"], "launches": st1["launches"] - st0["launches"],
+    }
+    # plain path: one FP64 solve per request, first come first served, same arrivals
+    ctx64 = {k: grt.grt_create(dict(v["problem"], precision="fp64"), dev) for k, v in probs.items()}
+    for k, v in probs.items():  # warm-up
+        d = v["problem"]["dim"]
+        grt.grt_solve(ctx64[k], np.zeros((2, d)), np.full(2, 0.5), np.full(2, 1000, np.uint64), v["K"], v["L"],
+                      v["M"], 99, want_coef=False, want_se=False)
+    plat, ppoints, ptrees = [], 0, 0.0
+    t0 = time.perf_counter()
+    for r in trace[:plain_requests]:
+        now = time.perf_counter() - t0
+        if now < r["arrival"]:
+            time.sleep(r["arrival"] - now)
+        v = probs[r["key"]]
+        grt.grt_solve(ctx64[r["key"]], r["x"], r["t"], r["ntrees"], v["K"], v["L"], v["M"], r["seed"],
+                      r["point_base"], want_coef=False, want_se=False)
+        plat.append(time.perf_counter() - t0 - r["arrival"])
+        ppoints += len(r["t"])
+        ptrees += float(r["ntrees"].sum())
+        if time.perf_counter() - t0 > plain_cap_s:
+            break
+    pwall = time.perf_counter() - t0
+    m = len(plat)
+    out["plain"] = {
+        "kind": "one FP64 grt_solve (walk + finalize launch) per request, first come first served, same arrivals",
+        "requests": m, "p50_ms": 1e3 * _pct(plat, 50), "p99_ms": 1e3 * _pct(plat, 99),
+        "points_per_s": ppoints / pwall, "trees_per_s": ptrees / pwall,
+        "batched_p50_ms_same_requests": 1e3 * _pct(lat[:m], 50),
+        "batched_p99_ms_same_requests": 1e3 * _pct(lat[:m], 99),
+    }
+    for c in list(ctxs.values()) + list(ctx64.values()):
+        c.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def gpu_arm(args) -> int:
@@ -422,6 +515,9 @@ def gpu_arm(args) -> int:
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "finite_output": finite,
     }
+    if not args.no_serving:
+        line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,
+                                        float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")))
     print(json.dumps(line))
@@ -439,6 +535,9 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--trees", type=int, default=0, help="trees per point (profiling cases; default: the workload's)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving trace")
+    ap.add_argument("--serving-requests", type=int, default=150)
+    ap.add_argument("--plain-requests", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

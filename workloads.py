@@ -169,3 +169,53 @@ def subsample(wl: dict, npoints: int, ntrees: int | None = None, stride: int | N
 
 def random_points(rng: np.random.Generator, n: int, dim: int, lo: float = -3.0, hi: float = 3.0) -> np.ndarray:
     return rng.uniform(lo, hi, size=(n, dim))
+
+
+# ----------------------------------------------------------------------------
+# serving trace: Poisson arrivals of point-solve requests
+# ----------------------------------------------------------------------------
+def serving_problems(precision: str = "fp32") -> dict:
+    """The nine request problems: f in {u^2 - u, sin u, u - u^3} x d in {1, 2, 3} (Strategy B).
+
+    Diffusion constants 1, 0.5, 0.1 for the three f; u0 as in the other workloads.
+    Series shapes: K = 8 [4/4], 10 [5/5], 12 [6/6].
+    """
+    out = {}
+    fs = {
+        "u2-u": ([0.0, -1.0, 1.0], "uniform", 1.0, lambda d: ("gauss", (0.5, 0.3) + (1 / math.sqrt(2.0),) + (0.0,) * d), 8),
+        "sin": (list(SIN9), "abs", 0.5, lambda d: ("gauss", (0.0, 1.2, 1.0) + (0.0,) * d), 10),
+        "u-u3": ([0.0, 1.0, 0.0, -1.0], "uniform", 0.1, lambda d: ("tanh_prod", (0.0, 1.0) + (0.3,) * d), 12),
+    }
+    for fname, (coef, law, D, u0, K) in fs.items():
+        for d in (1, 2, 3):
+            out[(fname, d)] = dict(problem=dict(dim=d, D=D, f_coef=list(coef), u0=u0(d), strategy="B",
+                                                q=default_q(coef, law), arity_law=law, precision=precision),
+                                   K=K, L=K // 2, M=K // 2)
+    return out
+
+
+def serving_trace(n_requests: int, rate_per_s: float, seed: int = 0, max_points: int = 4096,
+                  trees_lo: float = 1e3, trees_hi: float = 1e7) -> list:
+    """Seeded Poisson arrivals; points per request log-uniform in [1, max_points], tree budgets
+    per point log-uniform in [trees_lo, trees_hi], problem uniform over serving_problems()."""
+    rng = np.random.default_rng(seed)
+    keys = sorted(serving_problems().keys())
+    t_arr = 0.0
+    out = []
+    for k in range(n_requests):
+        t_arr += rng.exponential(1.0 / rate_per_s)
+        key = keys[int(rng.integers(0, len(keys)))]
+        n = int(np.clip(np.exp(rng.uniform(0.0, math.log(max_points))), 1, max_points))
+        d = key[1]
+        x = rng.uniform(-3.0, 3.0, size=(n, d))
+        t = rng.uniform(0.1, 1.0, size=n)
+        nt = np.exp(rng.uniform(math.log(trees_lo), math.log(trees_hi), size=n)).astype(np.uint64)
+        out.append(dict(arrival=t_arr, key=key, x=x, t=t, ntrees=nt, seed=k, point_base=0))
+    return out
+
+
+def serving_mean_trees(max_points: int = 4096, trees_lo: float = 1e3, trees_hi: float = 1e7) -> float:
+    """Expected trees per request of serving_trace (log-uniform points x log-uniform budgets)."""
+    mp = (max_points - 1) / math.log(max_points)
+    mt = (trees_hi - trees_lo) / math.log(trees_hi / trees_lo)
+    return mp * mt
