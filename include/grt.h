@@ -169,6 +169,30 @@ int grt_plan_timing(grt_plan *plan, float *walk_ms, float *finalize_ms);
 /* Number of kernel launches one grt_plan_execute enqueues. */
 int grt_plan_launches(const grt_plan *plan);
 
+/* Launch shape of the FP32 walk, cfg [4] = {warps per block (4 | 8), stack
+ * levels kept in shared memory (0 = all K | 3 = the top three, deeper ones in
+ * local memory), resident blocks per SM to launch (0 = all that fit), trees per
+ * work-queue chunk (multiple of 32)}.  The shape never changes a result: the
+ * same trees are walked and their records are binned in the same order.  The
+ * FP64 walk has one shape.  Default {4, 0, 0, 512}. */
+int grt_plan_set_config(grt_plan *plan, const int32_t *cfg);
+int grt_plan_get_config(const grt_plan *plan, int32_t *cfg);
+
+/* Autotuner (batching of uneven budgets): runs the plan on the
+ * given device buffers once per candidate shape (a warm run plus two timed runs,
+ * CUDA events on `stream`), keeps the fastest walk, and returns it in cfg_out
+ * [4] (may be NULL).  Leaves the outputs of a full solve in the buffers. */
+int grt_plan_autotune(grt_plan *plan, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                      double *d_u, double *d_coef, double *d_se, int32_t *d_status, void *stream, int32_t *cfg_out);
+
+/* CUDA graph of one execution of the plan on fixed device buffers (the
+ * arguments of grt_plan_execute): capture runs the plan once normally (on the
+ * context's own stream) and then records one execution into a graph owned by
+ * the plan; launch replays it on `stream`.  A new capture replaces the old. */
+int grt_plan_graph_capture(grt_plan *plan, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                           double *d_u, double *d_coef, double *d_se, int32_t *d_status);
+int grt_plan_graph_launch(grt_plan *plan, void *stream);
+
 /* Release a plan.  NULL is ignored. */
 void grt_plan_destroy(grt_plan *plan);
 

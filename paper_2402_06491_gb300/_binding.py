@@ -75,6 +75,11 @@ def _load():
         "grt_plan_set_timing": ([_vp, i32], i32),
         "grt_plan_timing": ([_vp, _P(ctypes.c_float), _P(ctypes.c_float)], i32),
         "grt_plan_launches": ([_vp], i32),
+        "grt_plan_set_config": ([_vp, i32p], i32),
+        "grt_plan_get_config": ([_vp, i32p], i32),
+        "grt_plan_autotune": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp, _vp, i32p], i32),
+        "grt_plan_graph_capture": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp], i32),
+        "grt_plan_graph_launch": ([_vp, _vp], i32),
         "grt_plan_destroy": ([_vp], None),
         "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
@@ -295,6 +300,43 @@ def grt_plan_timing(plan: Plan):
     return float(a.value), float(b.value)
 
 
+def grt_plan_set_config(plan: Plan, cfg) -> None:
+    """Walk launch shape [warps, smem stack levels, blocks per SM, trees per queue chunk]."""
+    c = np.ascontiguousarray(cfg, dtype=np.int32)
+    _check(_load().grt_plan_set_config(plan.handle, _ptr(c, ctypes.c_int32)), plan.ctx.handle)
+
+
+def grt_plan_get_config(plan: Plan) -> list:
+    c = np.zeros(4, np.int32)
+    _check(_load().grt_plan_get_config(plan.handle, _ptr(c, ctypes.c_int32)), plan.ctx.handle)
+    return [int(v) for v in c]
+
+
+def grt_plan_autotune(plan: Plan, x, t, seed: int, point_base: int, u, coef=None, se=None, status=None,
+                      stream=None) -> list:
+    """Time the candidate launch shapes on this plan's workload and keep the fastest; returns it."""
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    c = np.zeros(4, np.int32)
+    _check(_load().grt_plan_autotune(plan.handle, _devptr(x), _devptr(t), int(seed), int(point_base), _devptr(u),
+                                     _devptr(coef), _devptr(se), _devptr(status), sh, _ptr(c, ctypes.c_int32)),
+           plan.ctx.handle)
+    return [int(v) for v in c]
+
+
+def grt_plan_graph_capture(plan: Plan, x, t, seed: int, point_base: int, u, coef=None, se=None, status=None) -> None:
+    _check(_load().grt_plan_graph_capture(plan.handle, _devptr(x), _devptr(t), int(seed), int(point_base), _devptr(u),
+                                          _devptr(coef), _devptr(se), _devptr(status)), plan.ctx.handle)
+
+
+def grt_plan_graph_launch(plan: Plan, stream=None) -> None:
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(_load().grt_plan_graph_launch(plan.handle, sh), plan.ctx.handle)
+
+
 def grt_plan_launches(plan: Plan) -> int:
     return int(_load().grt_plan_launches(plan.handle))
 
@@ -441,5 +483,7 @@ def grt_server_stats(server: Server) -> dict:
 
 EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
+            "grt_plan_set_config", "grt_plan_get_config", "grt_plan_autotune", "grt_plan_graph_capture",
+            "grt_plan_graph_launch",
             "grt_pade", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats"]

@@ -51,7 +51,14 @@ struct grt_plan {
   int launches = 0;
   bool timing = false, timed_last = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  grt::WalkConfig cfg{};             // launch shape of the walk (autotuned or set)
+  cudaGraph_t graph = nullptr;       // a captured execution (grt_plan_graph_capture)
+  cudaGraphExec_t graph_exec = nullptr;
   void release() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    graph_exec = nullptr;
+    graph = nullptr;
     for (auto &e : ev)
       if (e) {
         cudaEventDestroy(e);
@@ -247,7 +254,7 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
     recs += (ntrees[i] + 3) & ~(uint64_t)3;
     cprefix[(size_t)i] = (uint32_t)chunks;
     chunks += ntrees[i] == 0 ? 1 : (ntrees[i] + grt::kBinChunk - 1) / grt::kBinChunk;
-    items += (ntrees[i] + grt::kTile - 1) / grt::kTile;
+    items += (ntrees[i] + p->cfg.tile - 1) / p->cfg.tile;
     trees += ntrees[i];
     nt32[(size_t)i] = (uint32_t)ntrees[i];
     if (items >= 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "too many work items (total trees too large)");
@@ -304,6 +311,7 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   w.prefix = p->prefix.as<uint32_t>();
   w.tree_prefix = p->tree_prefix.as<unsigned long long>();
   w.n = (int)p->n;
+  w.tile = p->cfg.tile;
   w.total_items = p->total_items;
   w.rec_w = p->rec_w.ptr;
   w.rec_o = p->rec_o.as<uint8_t>();
@@ -313,7 +321,7 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[0], stream));
   GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, p->work_bytes, stream));
   if (p->total_items > 0)
-    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
+    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, p->cfg, c->num_sms, stream));
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[1], stream));
   grt::FinalizeParams f{};
   f.rec_w = p->rec_w.ptr;
@@ -518,6 +526,121 @@ int grt_plan_timing(grt_plan *p, float *walk_ms, float *finalize_ms) {
 
 int grt_plan_launches(const grt_plan *p) { return p ? p->launches : 0; }
 
+int grt_plan_set_config(grt_plan *p, const int32_t *cfg) {
+  if (!p || !cfg) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if ((cfg[0] != 4 && cfg[0] != 8) || (cfg[1] != 0 && cfg[1] != 3) || cfg[2] < 0 || cfg[3] < 32 ||
+      cfg[3] > (1 << 20) || (cfg[3] & 31))
+    return c->set_error(GRT_EINVAL, "config: warps 4|8, smem_levels 0|3, blocks_per_sm >= 0, tile a multiple of 32");
+  if (p->n < 0) return c->set_error(GRT_EINVAL, "plan has no valid layout");
+  grt::WalkConfig nc;
+  nc.warps = cfg[0];
+  nc.smem_levels = cfg[1];
+  nc.blocks_per_sm = cfg[2];
+  nc.tile = (uint32_t)cfg[3];
+  if (nc.tile != p->cfg.tile) {  // the queue chunks change: lay the plan out again
+    const std::vector<uint64_t> nt = p->host_ntrees;
+    const grt::WalkConfig old = p->cfg;
+    p->cfg = nc;
+    p->n = -1;
+    const int rc = plan_configure(p, (int64_t)nt.size(), nt.data(), p->K, p->L, p->M);
+    if (rc != GRT_OK) {
+      p->cfg = old;
+      return rc;
+    }
+  }
+  p->cfg = nc;
+  return GRT_OK;
+}
+
+int grt_plan_get_config(const grt_plan *p, int32_t *cfg) {
+  if (!p || !cfg) return GRT_EINVAL;
+  cfg[0] = p->cfg.warps;
+  cfg[1] = p->cfg.smem_levels;
+  cfg[2] = p->cfg.blocks_per_sm;
+  cfg[3] = (int32_t)p->cfg.tile;
+  return GRT_OK;
+}
+
+int grt_plan_autotune(grt_plan *p, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                      double *d_u, double *d_coef, double *d_se, int32_t *d_status, void *stream, int32_t *cfg_out) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (p->n <= 0 || c->pb.precision == GRT_FP64) {  // nothing to time / the FP64 walk has one launch shape  // the FP64 walk has one launch shape
+    if (cfg_out) grt_plan_get_config(p, cfg_out);
+    return GRT_OK;
+  }
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  const bool had_timing = p->timing;
+  int rc = grt_plan_set_timing(p, 1);
+  if (rc != GRT_OK) return rc;
+  static const int32_t cand[][4] = {{4, 0, 0, 512},  {4, 3, 0, 512},  {8, 0, 0, 512},  {8, 3, 0, 512},
+                                    {4, 0, 0, 2048}, {4, 3, 0, 2048}, {8, 0, 0, 2048}, {8, 3, 0, 2048},
+                                    {4, 0, 4, 512},  {4, 3, 8, 512}};
+  int32_t best[4];
+  grt_plan_get_config(p, best);
+  float best_ms = 1e30f;
+  for (const auto &cf : cand) {
+    if ((rc = grt_plan_set_config(p, cf)) != GRT_OK) break;
+    float wm = 0.f, fm = 0.f, tot = 0.f;
+    for (int rep = 0; rep < 3 && rc == GRT_OK; ++rep) {  // first run warms the variant up
+      rc = grt_plan_execute(p, d_x, d_t, seed, point_base, d_u, d_coef, d_se, d_status, stream);
+      if (rc == GRT_OK) rc = grt_plan_timing(p, &wm, &fm);
+      if (rep > 0) tot += wm;
+    }
+    if (rc != GRT_OK) break;
+    if (tot < best_ms) {
+      best_ms = tot;
+      std::memcpy(best, cf, sizeof(best));
+    }
+  }
+  const int rc2 = grt_plan_set_config(p, best);
+  grt_plan_set_timing(p, had_timing ? 1 : 0);
+  if (rc != GRT_OK) return rc;
+  if (rc2 != GRT_OK) return rc2;
+  if (cfg_out) std::memcpy(cfg_out, best, sizeof(best));
+  return GRT_OK;
+}
+
+int grt_plan_graph_capture(grt_plan *p, const double *d_x, const double *d_t, uint64_t seed, uint64_t point_base,
+                           double *d_u, double *d_coef, double *d_se, int32_t *d_status) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (p->n < 0) return c->set_error(GRT_EINVAL, "plan has no valid layout");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  // one plain execution first: kernels and their attributes are loaded outside the capture
+  int rc = plan_execute(p, d_x, d_t, seed, point_base, d_u, d_coef, d_se, d_status, c->stream);
+  if (rc != GRT_OK) return rc;
+  GRT_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->graph_exec = nullptr;
+  p->graph = nullptr;
+  GRT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  rc = plan_execute(p, d_x, d_t, seed, point_base, d_u, d_coef, d_se, d_status, c->stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc != GRT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return c->cuda_error(e, "cudaStreamEndCapture");
+  p->graph = g;
+  GRT_CUDA(c, cudaGraphInstantiate(&p->graph_exec, g, 0));
+  return GRT_OK;
+}
+
+int grt_plan_graph_launch(grt_plan *p, void *stream) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (!p->graph_exec) return c->set_error(GRT_EINVAL, "no captured graph on this plan");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  GRT_CUDA(c, cudaGraphLaunch(p->graph_exec, (cudaStream_t)stream));
+  p->last_stream = (cudaStream_t)stream;
+  p->timed_last = p->timing;
+  return GRT_OK;
+}
+
 void grt_plan_destroy(grt_plan *p) {
   if (!p) return;
   cudaSetDevice(p->ctx->device);
@@ -719,6 +842,7 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
   w.prefix = reinterpret_cast<const uint32_t *>(base + kNaPrefix);
   w.tree_prefix = reinterpret_cast<const unsigned long long *>(base + kNaTreePrefix);
   w.n = (int)n;
+  w.tile = grt::kTile;
   w.total_items = (uint32_t)items;
   w.rec_w = base + kNaRecW;
   w.rec_o = base + kNaRecO;
@@ -726,7 +850,7 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
   w.stats = reinterpret_cast<unsigned long long *>(base + kNaWork + 8);
   const bool fp64 = c->pb.precision == GRT_FP64;
   if (items > 0)
-    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, c->num_sms, stream, nullptr, nullptr));
+    GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, grt::WalkConfig{}, c->num_sms, stream));
   grt::FinalizeParams f{};
   f.rec_w = w.rec_w;
   f.rec_o = w.rec_o;

@@ -14,10 +14,9 @@ namespace grt {
 
 constexpr int kMaxTerms = 16;     // powers 0..15 of f
 constexpr int kMaxK = 16;         // highest series order
-constexpr int kTile = 512;        // trees per work-queue chunk
+constexpr int kTile = 512;        // default trees per work-queue chunk
 constexpr int kFinThreads = 128;  // threads of a finalize (binning) block
 constexpr int kBinChunk = 8192;   // tree records binned by one finalize block
-constexpr int kWarpsPerBlock = 4; // persistent walk kernel
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4 };
@@ -54,6 +53,7 @@ struct WalkParams {
   const uint32_t *tree_first;  // [n] first tree index walked for each point, or null (0): incremental solves
   const uint32_t *point_id;    // [n] random-stream point index of each point, or null (point_base + p)
   int n;
+  uint32_t tile;             // trees per queue chunk
   uint32_t total_items;      // queue chunks
   void *rec_w;               // [total trees] tree weights (float or double)
   uint8_t *rec_o;            // [total trees] tree orders (K+1 = pruned)

@@ -33,8 +33,16 @@ struct FinalizeParams {
   unsigned long long *stats; // [1] splitting events, [2] pruned trees (added here)
 };
 
-cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, int num_sms, cudaStream_t stream,
-                        int *grid_out, size_t *smem_out);
+// Launch shape of the walk kernel (results do not depend on it).
+struct WalkConfig {
+  int warps = 4;          // warps per block: 4 or 8
+  int smem_levels = 0;    // stack levels in shared memory: 0 = all K, 3 = top three (rest local)
+  int blocks_per_sm = 0;  // resident blocks per SM to launch (0 = as many as fit)
+  uint32_t tile = 512;    // trees per work-queue chunk
+};
+
+cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms,
+                        cudaStream_t stream);
 cudaError_t launch_trees(bool fp64, int dim, int strategy, const WalkParams &p, const double *x0, double t0,
                          uint32_t point, uint32_t first, uint32_t ntrees, int32_t *order, double *w, uint32_t *nodes,
                          uint64_t *hash, cudaStream_t stream);

@@ -265,6 +265,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     w.tree_first = d_first;
     w.point_id = d_pid;
     w.n = (int)n;
+    w.tile = grt::kTile;
     w.total_items = (uint32_t)items;
     w.rec_w = rec_w.ptr;
     w.rec_o = rec_o.as<uint8_t>();
@@ -272,7 +273,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     w.stats = reinterpret_cast<unsigned long long *>(work.as<unsigned char>() + 8);
     const bool fp64 = c->pb.precision == GRT_FP64;
     if (items > 0) {
-      e = grt::launch_walk(fp64, dim, c->pb.strategy, w, num_sms, stream, nullptr, nullptr);
+      e = grt::launch_walk(fp64, dim, c->pb.strategy, w, grt::WalkConfig{}, num_sms, stream);
       ++launches;
     }
     grt::FinalizeParams f{};

@@ -21,14 +21,22 @@
 
 namespace grt {
 
-// Shared-memory stack of one warp: per level and lane the frame
-// (y[DIM], tau, child label base lo/hi, (k << 8) | next digit), laid out
-// field-major [field][level][lane] so that a warp's access to its lanes'
-// frames touches 32 distinct banks whatever the lanes' depths.
+// Stack of pending frames, one per split with children still to walk:
+// (y[DIM], tau, child label base lo/hi, (k << 8) | next digit).  Shared-memory
+// levels are laid out field-major [field][level][lane] so that a warp's access
+// to its lanes' frames touches 32 distinct banks whatever the lanes' depths.
+// SLEV = 0 keeps every level (K of them) in shared memory; SLEV > 0 keeps the
+// top SLEV levels there and deeper ones (rare: a frame is pushed only for
+// splits of arity >= 2) in per-thread local memory, for more resident warps.
+__host__ __device__ inline int smem_levels(int K, int slev) {
+  const int k = K > 0 ? K : 1;
+  return slev > 0 && slev < k ? slev : k;
+}
+
 template <typename Real, int DIM>
-__host__ __device__ inline size_t warp_stack_bytes(int K) {
-  const int levels = K > 0 ? K : 1;
-  return (((size_t)levels * 32 * ((DIM + 1) * sizeof(Real) + 3 * sizeof(uint32_t))) + 15) & ~(size_t)15;
+__host__ __device__ inline size_t warp_stack_bytes(int K, int slev) {
+  return (((size_t)smem_levels(K, slev) * 32 * ((DIM + 1) * sizeof(Real) + 3 * sizeof(uint32_t))) + 15) &
+         ~(size_t)15;
 }
 
 // Point owning queue chunk g: the largest p with prefix[p] <= g, found by a
@@ -46,8 +54,8 @@ __device__ __forceinline__ int find_point(const uint32_t *__restrict__ prefix, i
   return lo;
 }
 
-template <typename Real, int DIM, int STRAT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkParams p) {
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV>
+__global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Real s_factor[kMaxTerms];
   __shared__ int s_arity[kMaxTerms];
@@ -61,8 +69,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = p.K;
-  const int lv = K > 0 ? K : 1;
-  unsigned char *wb = smem + (size_t)warp * warp_stack_bytes<Real, DIM>(K);
+  const int lv = smem_levels(K, SLEV);  // shared-memory levels
+  unsigned char *wb = smem + (size_t)warp * warp_stack_bytes<Real, DIM>(K, SLEV);
+  constexpr int LL = SLEV > 0 ? kMaxK : 1;  // local-memory levels (unused when SLEV = 0)
+  Real ly[LL][DIM], ltau[LL];
+  uint32_t llo[LL], lhi[LL], lnk[LL];
   Real *stk_y = reinterpret_cast<Real *>(wb);             // [DIM][lv][32]
   Real *stk_tau = stk_y + (size_t)DIM * lv * 32;          // [lv][32]
   uint32_t *stk_lo = reinterpret_cast<uint32_t *>(stk_tau + (size_t)lv * 32);
@@ -109,8 +120,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
           }
           const int pt = find_point(p.prefix, p.n, item, lane);
           const uint32_t N = __ldg(p.ntrees + pt);
-          c_next = (item - __ldg(p.prefix + pt)) * (uint32_t)kTile;
-          c_end = min(c_next + (uint32_t)kTile, N);
+          c_next = (item - __ldg(p.prefix + pt)) * p.tile;
+          c_end = min(c_next + p.tile, N);
           c_point = p.point_id ? __ldg(p.point_id + pt) : p.point_base + (uint32_t)pt;
           c_first = p.tree_first ? __ldg(p.tree_first + pt) : 0u;
           c_rec = __ldg(p.tree_prefix + pt);
@@ -167,13 +178,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
     const int k = (split && !pruned) ? s_arity[o.cat] : 0;
     const bool down = k > 0;
     if (k > 1) {  // remember the remaining children 2 .. k: labels 16 id + 2 .. 16 id + k
-      const int at = depth * 32 + lane;
+      const uint32_t clo = id_lo << 4, chi = __funnelshift_l(id_lo, id_hi, 4), cnk = ((uint32_t)k << 8) | 2u;
+      if (SLEV == 0 || depth < lv) {
+        const int at = depth * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
-      stk_tau[at] = o.tau_c;
-      stk_lo[at] = id_lo << 4;
-      stk_hi[at] = __funnelshift_l(id_lo, id_hi, 4);
-      stk_nk[at] = ((uint32_t)k << 8) | 2u;
+        for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
+        stk_tau[at] = o.tau_c;
+        stk_lo[at] = clo;
+        stk_hi[at] = chi;
+        stk_nk[at] = cnk;
+      } else {
+        const int at = depth - lv;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) ly[at][i] = o.y[i];
+        ltau[at] = o.tau_c;
+        llo[at] = clo;
+        lhi[at] = chi;
+        lnk[at] = cnk;
+      }
       ++depth;
     }
     const bool up = !down && !pruned && depth > 0;
@@ -185,16 +207,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) walk_kernel(const WalkPar
       id_lo = (id_lo << 4) | 1u;
     }
     if (up) {
-      const int at = (depth - 1) * 32 + lane;
+      const int lvl = depth - 1;
+      uint32_t nk, clo;
+      if (SLEV == 0 || lvl < lv) {
+        const int at = lvl * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
-      tau = stk_tau[at];
-      const uint32_t nk = stk_nk[at];
+        for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
+        tau = stk_tau[at];
+        nk = stk_nk[at];
+        clo = stk_lo[at];
+        id_hi = stk_hi[at];
+        if ((nk & 0xFFu) != (nk >> 8)) stk_nk[at] = nk + 1u;
+      } else {
+        const int at = lvl - lv;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) x[i] = ly[at][i];
+        tau = ltau[at];
+        nk = lnk[at];
+        clo = llo[at];
+        id_hi = lhi[at];
+        if ((nk & 0xFFu) != (nk >> 8)) lnk[at] = nk + 1u;
+      }
       const uint32_t nd = nk & 0xFFu;
-      id_lo = stk_lo[at] | nd;
-      id_hi = stk_hi[at];
+      id_lo = clo | nd;
       if (nd == (nk >> 8)) --depth;
-      else stk_nk[at] = nk + 1u;
     }
     if (!down && !up) {  // leaf with nothing pending, or pruned
       reinterpret_cast<Real *>(p.rec_w)[rec] = pruned ? Real(0) : W;
@@ -290,34 +326,45 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-template <typename Real, int DIM, int STRAT>
-static cudaError_t launch_walk_t(const WalkParams &p, int num_sms, cudaStream_t stream, int *grid_out,
-                                 size_t *smem_out) {
-  const size_t smem = warp_stack_bytes<Real, DIM>(p.K) * kWarpsPerBlock;
-  auto kern = walk_kernel<Real, DIM, STRAT>;
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV>
+static cudaError_t launch_walk_t(const WalkParams &p, const WalkConfig &cfg, int num_sms, cudaStream_t stream) {
+  const size_t smem = warp_stack_bytes<Real, DIM>(p.K, SLEV) * WARPS;
+  auto kern = walk_kernel<Real, DIM, STRAT, WARPS, SLEV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
   long grid = (long)per_sm * num_sms;
-  const long need = ((long)p.total_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const long need = ((long)p.total_items + WARPS - 1) / WARPS;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  if (grid_out) *grid_out = (int)grid;
-  if (smem_out) *smem_out = smem;
-  kern<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(p);
+  kern<<<(unsigned)grid, WARPS * 32, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, int num_sms, cudaStream_t stream,
-                        int *grid_out, size_t *smem_out) {
+template <typename Real, int DIM, int STRAT>
+static cudaError_t launch_walk_cfg(const WalkParams &p, const WalkConfig &cfg, int num_sms, cudaStream_t stream) {
+  if (cfg.warps == 8 && cfg.smem_levels == 3) return launch_walk_t<Real, DIM, STRAT, 8, 3>(p, cfg, num_sms, stream);
+  if (cfg.warps == 8) return launch_walk_t<Real, DIM, STRAT, 8, 0>(p, cfg, num_sms, stream);
+  if (cfg.smem_levels == 3) return launch_walk_t<Real, DIM, STRAT, 4, 3>(p, cfg, num_sms, stream);
+  return launch_walk_t<Real, DIM, STRAT, 4, 0>(p, cfg, num_sms, stream);
+}
+
+cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms,
+                        cudaStream_t stream) {
 #define GRT_WALK_CASE(R, D, S) \
-  if (dim == D && strategy == S) return launch_walk_t<R, D, S>(p, num_sms, stream, grid_out, smem_out);
-  if (fp64) {
-    GRT_WALK_CASE(double, 1, kStratA) GRT_WALK_CASE(double, 2, kStratA) GRT_WALK_CASE(double, 3, kStratA)
-    GRT_WALK_CASE(double, 1, kStratB) GRT_WALK_CASE(double, 2, kStratB) GRT_WALK_CASE(double, 3, kStratB)
+  if (dim == D && strategy == S) return launch_walk_cfg<R, D, S>(p, cfg, num_sms, stream);
+  if (fp64) {  // the FP64 walk runs in the default configuration
+    const WalkConfig dflt{};
+    if (dim == 1 && strategy == kStratA) return launch_walk_t<double, 1, kStratA, 4, 0>(p, dflt, num_sms, stream);
+    if (dim == 2 && strategy == kStratA) return launch_walk_t<double, 2, kStratA, 4, 0>(p, dflt, num_sms, stream);
+    if (dim == 3 && strategy == kStratA) return launch_walk_t<double, 3, kStratA, 4, 0>(p, dflt, num_sms, stream);
+    if (dim == 1 && strategy == kStratB) return launch_walk_t<double, 1, kStratB, 4, 0>(p, dflt, num_sms, stream);
+    if (dim == 2 && strategy == kStratB) return launch_walk_t<double, 2, kStratB, 4, 0>(p, dflt, num_sms, stream);
+    if (dim == 3 && strategy == kStratB) return launch_walk_t<double, 3, kStratB, 4, 0>(p, dflt, num_sms, stream);
   } else {
     GRT_WALK_CASE(float, 1, kStratA) GRT_WALK_CASE(float, 2, kStratA) GRT_WALK_CASE(float, 3, kStratA)
     GRT_WALK_CASE(float, 1, kStratB) GRT_WALK_CASE(float, 2, kStratB) GRT_WALK_CASE(float, 3, kStratB)

@@ -1,0 +1,86 @@
+"""Batching of uneven budgets: launch shapes, the autotuner and CUDA graphs.
+
+The walk's launch shape (warps per block, stack levels in shared memory, blocks
+per SM, queue chunk size) must never change a result: the same trees are
+walked and their records binned in the same order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [[4, 0, 0, 512], [4, 3, 0, 512], [8, 0, 0, 512], [8, 3, 0, 2048], [4, 0, 2, 64], [8, 3, 1, 4096]]
+
+
+@pytest.fixture(scope="module")
+def grt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2402_06491_gb300 as pkg
+
+    return pkg
+
+
+def _device_case(grt, wl):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    n, K = wl["x"].shape[0], wl["K"]
+    bufs = dict(x=torch.from_numpy(wl["x"]).to(dev), t=torch.from_numpy(wl["t"]).to(dev),
+                u=torch.empty(n, dtype=torch.float64, device=dev),
+                coef=torch.empty((n, K + 1), dtype=torch.float64, device=dev),
+                status=torch.empty(n, dtype=torch.int32, device=dev))
+    return torch, bufs
+
+
+@pytest.mark.parametrize("name", ["uneven_2d", "pdd_3d"])
+def test_every_launch_shape_gives_the_same_bits(grt, name):
+    wl = workloads.subsample(workloads.WORKLOADS[name](), 96, ntrees=20000)
+    torch, b = _device_case(grt, wl)
+    ctx = grt.grt_create(wl["problem"], 0)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], wl["K"], wl["L"], wl["M"])
+    outs = []
+    for shape in SHAPES:
+        grt.grt_plan_set_config(plan, shape)
+        assert grt.grt_plan_get_config(plan) == shape
+        grt.grt_plan_execute(plan, b["x"], b["t"], 3, 0, b["u"], b["coef"], None, b["status"])
+        torch.cuda.synchronize()
+        outs.append((b["u"].cpu().numpy().copy(), b["coef"].cpu().numpy().copy(), b["status"].cpu().numpy().copy()))
+    for u, c, s in outs[1:]:
+        assert np.array_equal(c, outs[0][1]) and np.array_equal(s, outs[0][2])
+        assert np.array_equal(u, outs[0][0], equal_nan=True)
+    o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], 3)
+    scale = np.maximum(np.abs(o["u"]), np.abs(o["coef"]).sum(axis=1))
+    assert np.all(np.abs(outs[0][0] - o["u"]) <= 1e-5 * scale)
+    with pytest.raises(grt.GrtError):
+        grt.grt_plan_set_config(plan, [5, 0, 0, 512])
+    plan.close()
+    ctx.close()
+
+
+def test_autotuner_and_graph(grt):
+    wl = workloads.subsample(workloads.workload_uneven_2d(), 512, ntrees=200000)
+    torch, b = _device_case(grt, wl)
+    ctx = grt.grt_create(wl["problem"], 0)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], wl["K"], wl["L"], wl["M"])
+    grt.grt_plan_execute(plan, b["x"], b["t"], 0, 0, b["u"], b["coef"], None, b["status"])
+    torch.cuda.synchronize()
+    ref = b["coef"].cpu().numpy().copy()
+    cfg = grt.grt_plan_autotune(plan, b["x"], b["t"], 0, 0, b["u"], b["coef"], None, b["status"])
+    assert cfg[0] in (4, 8) and cfg[1] in (0, 3) and grt.grt_plan_get_config(plan) == cfg
+    torch.cuda.synchronize()
+    assert np.array_equal(b["coef"].cpu().numpy(), ref)
+    b["coef"].zero_()
+    grt.grt_plan_graph_capture(plan, b["x"], b["t"], 0, 0, b["u"], b["coef"], None, b["status"])
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        b["coef"].zero_()
+        torch.cuda.synchronize()
+        grt.grt_plan_graph_launch(plan, s)
+        s.synchronize()
+        assert np.array_equal(b["coef"].cpu().numpy(), ref)
+    plan.close()
+    ctx.close()
