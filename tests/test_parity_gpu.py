@@ -40,8 +40,26 @@ def _solve_both(grt, pb, x, t, nt, K, L, M, seed, point_base=0):
 FP32_FLOOR = 1e-30  # coefficients below this are outside what an FP32 walk represents
 
 
-def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5):
-    """Pade value within rtol * max(|u|, sum |a_n|); a_n within ctol of the mean |W| of its order."""
+def pade_error_bound(a, L, M, da):
+    """First-order error of the Pade value from coefficient errors da (the Wuytack bound
+    ||P_f - P_f'|| <= K ||c - c'||, Sec. 2.4): sum_n |d u / d a_n| da_n, by central differences."""
+    a = np.asarray(a, float)
+    b = 0.0
+    for n in range(L + M + 1):
+        h = 1e-6 * max(abs(a[n]), 1e-12 * np.abs(a).max(), 1e-300)
+        ap, am = a.copy(), a.copy()
+        ap[n] += h
+        am[n] -= h
+        up, _, _ = oracle.pade(ap, L, M)
+        um, _, _ = oracle.pade(am, L, M)
+        b += abs((up - um) / (2 * h)) * da[n]
+    return b
+
+
+def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5, L=None, M=None):
+    """Pade value within rtol * max(|u|, sum |a_n|) -- or, where the Pade is ill-conditioned (past
+    blow-up, near a pole), within twice its first-order error bound from the coefficient budget;
+    a_n within ctol of the mean |W| of its order."""
     N = np.maximum(np.asarray(nt, float), 1.0)[:, None]
     scale_coef = o["sa"] / N  # mean |W| of each order: the natural scale of a_n
     err_c = np.abs(g["coef"] - o["coef"])
@@ -50,6 +68,16 @@ def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5):
     du = np.abs(g["u"] - o["u"])
     ratio_u = du / np.maximum(scale_u, 1e-300)
     bad_u = np.where(~(du <= rtol * scale_u))[0]
+    K = o["coef"].shape[1] - 1
+    if L is None:
+        L, M = K // 2, K - K // 2
+    conditioned = []
+    for i in bad_u:
+        bound = pade_error_bound(o["coef"][i], L, M, ctol * scale_coef[i] + FP32_FLOOR)
+        if du[i] <= 2.0 * bound:
+            conditioned.append(int(i))
+    bad_u = np.array([i for i in bad_u if int(i) not in conditioned], dtype=int)
+    assert len(conditioned) <= max(2, len(du) // 4), conditioned
     bad_c = np.argwhere(~(err_c <= ctol * scale_coef + FP32_FLOOR))
     high = (g["status"] & 8) != (o["status"] & 8)
     msg = (f"max u ratio {np.max(ratio_u):.3g}, max coef ratio {np.max(ratio_c):.3g}; "
@@ -60,6 +88,7 @@ def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5):
     # Pade degeneracy decisions (G9 reading) may differ only where the coefficients differ
     pade_diff = (g["status"] & 3) != (o["status"] & 3)
     assert pade_diff.sum() <= max(1, len(pade_diff) // 50), msg
+    return conditioned
 
 
 # ---------------------------------------------------------------------------
@@ -139,7 +168,7 @@ def test_kpp_1d_full_workload_fp64(grt):
 def test_point_solve_fp32(grt, name, ntrees, ctol):
     wl = workloads.subsample(workloads.WORKLOADS[name](), 24, ntrees=ntrees)
     g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
-    _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol)
+    _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol, L=wl["L"], M=wl["M"])
 
 
 def test_edge_budgets_and_orders(grt):
@@ -149,7 +178,7 @@ def test_edge_budgets_and_orders(grt):
     t = np.linspace(0.1, 1.0, nt.size)
     for K, L, M in [(10, 5, 5), (0, 0, 0), (3, 1, 2), (16, 0, 16)]:
         g, o = _solve_both(grt, pb, x, t, nt, K, L, M, 123)
-        _assert_fp32_parity(g, o, nt)
+        _assert_fp32_parity(g, o, nt, L=L, M=M)
         assert g["u"][0] == 0.0 and np.all(g["coef"][0] == 0.0)
 
 
@@ -251,4 +280,4 @@ def test_full_size_sin_2d_sampled_points(grt):
         o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], wl["K"], wl["L"],
                          wl["M"], wl["seed"], point_base=i)
         gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
-        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1])
+        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], L=wl["L"], M=wl["M"])
