@@ -250,6 +250,50 @@ def reference_arm(args) -> int:
 
 
 # ---------------------------------------------------------------------------
+# the other workloads: uneven budgets (4096 interface points) and the 3-D PDD planes
+# ---------------------------------------------------------------------------
+def workload_bench(grt, dev_index: int, name: str, steps: int) -> dict:
+    import torch
+
+    dev = torch.device("cuda", dev_index)
+    wl = workloads.WORKLOADS[name]()
+    n, K = wl["x"].shape[0], wl["K"]
+    ctx = grt.grt_create(wl["problem"], dev_index)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, wl["L"], wl["M"])
+    x = torch.from_numpy(wl["x"]).to(dev)
+    t = torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    cfg = grt.grt_plan_autotune(plan, x, t, wl["seed"], 0, u, coef, None, st, stream=s)
+    grt.grt_plan_set_timing(plan, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    wms, fms = [], []
+    for a, b in ev:
+        with torch.cuda.stream(s):
+            flush.zero_()
+        a.record(s)
+        grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, st, stream=s)
+        b.record(s)
+        wm, fm = grt.grt_plan_timing(plan)
+        wms.append(wm)
+        fms.append(fm)
+    torch.cuda.synchronize(dev)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    nodes, splits, pruned = grt.grt_plan_counters(plan)
+    trees = float(np.sum(wl["ntrees"]))
+    finite = bool(torch.isfinite(u).all().item())
+    plan.close()
+    ctx.close()
+    return {"trees_per_s": trees / (ms / 1e3), "points_per_s": n / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+            "walk_ms": float(np.mean(wms)), "finalize_ms": float(np.mean(fms)), "points": n, "trees": trees,
+            "nodes": nodes, "pruned_trees": pruned, "K": K, "L": wl["L"], "M": wl["M"],
+            "walk_config": dict(zip(["warps", "smem_levels", "blocks_per_sm", "tile"], cfg)), "finite_output": finite}
+
+
+# ---------------------------------------------------------------------------
 # serving: Poisson trace through the continuous-batching server vs the plain path
 # ---------------------------------------------------------------------------
 def _pct(v, q):
@@ -389,6 +433,9 @@ def gpu_arm(args) -> int:
     def step():
         grt.grt_plan_execute(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
 
+    walk_cfg = grt.grt_plan_autotune(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
+    stream.synchronize()
+
     for _ in range(max(args.warmup, 0)):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -434,6 +481,18 @@ def gpu_arm(args) -> int:
     time.sleep(0.3)
     sampler.stop()
     clocks = sampler.summary(t_wall0 - 0.05, t_wall1 + 0.05)
+
+    # the same step replayed from a CUDA graph of one execution
+    grt.grt_plan_graph_capture(plan, x, t, wl["seed"], point_base, u, coef, None, status)
+    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in g_ev:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a.record(stream)
+        grt.grt_plan_graph_launch(plan, stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = float(np.mean([a.elapsed_time(b) for a, b in g_ev]))
 
     # parity spot check of this run's output (rank 0's first points) is in the test suite; here the
     # result must at least be finite
@@ -506,6 +565,8 @@ def gpu_arm(args) -> int:
                     f" + {model['leaf']}/leaf x {nodes - splits} + {model['split']}/split x {splits}"
                     f" + {model['tree']}/tree x {int(trees_per_step)}",
             "walk_ms": walk_avg_ms, "finalize_ms": float(np.mean(fin_ms)),
+            "walk_config": dict(zip(["warps", "smem_levels", "blocks_per_sm", "tile"], walk_cfg)),
+            "graph_ms_per_step": graph_ms,
             "peak_basis": f"{SM_COUNT_GB300} SMs x 4 issue slots/clk x 32 threads x {sm_max:.0f} MHz (max SM clock)",
         },
         "e2e": ({"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
@@ -515,6 +576,15 @@ def gpu_arm(args) -> int:
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "finite_output": finite,
     }
+    if not args.no_workloads:
+        line["workloads"] = {
+            "uneven_2d": dict(workload_bench(grt, local, "uneven_2d", 5), description=(
+                "2-D u_t = Lap u + u^2, u0 = 1.5 + 0.5 cos x cos y, 4096 points on 64 interface segments of the 8x8 "
+                "split of [0,8]^2, t ~ U[0.1, 2], budgets log-uniform in [1e3, 1e6] (5.9e8 trees), K = 16, [8/8]")),
+            "pdd_3d": dict(workload_bench(grt, local, "pdd_3d", 3), description=(
+                "3-D u_t = 0.1 Lap u + u - u^3, u0 = prod tanh(x_i - 2), 9 interior planes x 32^2 nodes of the "
+                "4x4x4 split of [0,4]^3, t = 1, 1e5 trees per point (9.2e8 trees), K = 12, [6/6]")),
+        }
     if not args.no_serving:
         line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,
                                         float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
@@ -536,6 +606,7 @@ def main() -> int:
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--trees", type=int, default=0, help="trees per point (profiling cases; default: the workload's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving trace")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the uneven_2d and pdd_3d lines")
     ap.add_argument("--serving-requests", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=20)
     args = ap.parse_args()
