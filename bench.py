@@ -433,7 +433,11 @@ def gpu_arm(args) -> int:
     def step():
         grt.grt_plan_execute(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
 
-    walk_cfg = grt.grt_plan_autotune(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
+    if args.walk_config:
+        walk_cfg = tuple(int(v) for v in args.walk_config.split(","))
+        grt.grt_plan_set_config(plan, list(walk_cfg))
+    else:
+        walk_cfg = grt.grt_plan_autotune(plan, x, t, wl["seed"], point_base, u, coef, None, status, stream=stream)
     stream.synchronize()
 
     for _ in range(max(args.warmup, 0)):
@@ -607,6 +611,8 @@ def main() -> int:
     ap.add_argument("--trees", type=int, default=0, help="trees per point (profiling cases; default: the workload's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving trace")
     ap.add_argument("--no-workloads", action="store_true", help="skip the uneven_2d and pdd_3d lines")
+    ap.add_argument("--walk-config", default="",
+                    help="fixed walk launch shape 'warps,smem_levels,blocks_per_sm,tile' instead of the autotuner")
     ap.add_argument("--serving-requests", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=20)
     args = ap.parse_args()

@@ -19,6 +19,10 @@ Problem descriptions are plain dicts (see ``workloads.py``):
     lam, c_pot Strategy A clock rate and pulled-out potential
     q          Strategy B leaf probability
     arity_law  "uniform" (paper, Sec. 2.1 after Eq. probexp2) or "abs" (p_k ~ |b_k|)
+    coef       optional (kind, params, powers): variable coefficients c_k(x, t) = b_k gamma(x, t)
+               for k in powers (Sec. 1, Eq. nonlinear_new; Example 5); kinds
+               "gauss_over_t" exp(-sum w_i (x_i - m_i)^2) / (t + t0), params (w0, w1, w2, m0, m1, m2, t0),
+               and "gauss" exp(-sum w_i (x_i - m_i)^2), params (w0, w1, w2, m0, m1, m2)
 """
 from __future__ import annotations
 
@@ -41,6 +45,7 @@ STATUS_SERIES_PARTIAL = 4
 STATUS_HIGH_PRUNE = 8
 
 _U0_KINDS = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4}
+_COEF_KINDS = {"const": 0, "gauss_over_t": 1, "gauss": 2}
 
 
 class _OrProblem(ctypes.Structure):
@@ -56,6 +61,10 @@ class _OrProblem(ctypes.Structure):
         ("c_pot", ctypes.c_double),
         ("q", ctypes.c_double),
         ("arity_law", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("coef_kind", ctypes.c_int32),
+        ("coef_param", ctypes.c_double * 8),
+        ("coef_mask", ctypes.c_uint32),
     ]
 
 
@@ -124,6 +133,12 @@ def _problem(pb: dict) -> _OrProblem:
     s.c_pot = float(pb.get("c_pot", 0.0))
     s.q = float(pb.get("q", 0.5))
     s.arity_law = {"uniform": 0, "abs": 1}[pb.get("arity_law", "uniform")]
+    if "coef" in pb:
+        kind, params, powers = pb["coef"]
+        s.coef_kind = _COEF_KINDS[kind]
+        for i, v in enumerate(params):
+            s.coef_param[i] = float(v)
+        s.coef_mask = sum(1 << int(k) for k in powers)
     return s
 
 

@@ -41,6 +41,10 @@
  *             (Sec. 2.1 end, Sec. 2.4), after an eps-rescaling that leaves
  *             the approximant unchanged.
  *   Errors    per-order standard errors (Sec. 2.4, Eq. simplecase_discrete).
+ *   Variable coefficients  c_k(x, t) = b_k gamma(x, t) for the terms of a
+ *             mask (Sec. 1, Eq. nonlinear_new; Example 5): the split weight
+ *             is multiplied by gamma at the split position and at the PDE
+ *             time left to the children (Sec. 2.1, Eq. probexp1).
  *
  * Brownian increments.  For L = D*Lap the Green's function (Eqs. green,
  * SDE) is the Gaussian kernel of variance 2 D tau per coordinate, so each
@@ -85,10 +89,15 @@ typedef struct {
     double c_pot;
     double q;
     int32_t arity_law; /* 0 = uniform over the terms, 1 = p_k ~ |b_k| */
+    int32_t precision; /* unused by the oracle (always FP64); keeps the field order */
+    int32_t coef_kind; /* variable coefficients: 0 none, 1 gauss / (t + t0), 2 gauss */
+    double coef_param[8];
+    uint32_t coef_mask; /* bit k: c_k(x, t) = b_k gamma(x, t) */
 } or_problem;
 
 enum { OR_U0_CONST = 0, OR_U0_GAUSS = 1, OR_U0_COS_PROD = 2, OR_U0_TANH_PROD = 3, OR_U0_LOGISTIC = 4 };
 enum { OR_STRAT_A = 0, OR_STRAT_B = 1 };
+enum { OR_COEF_CONST = 0, OR_COEF_GAUSS_OVER_T = 1, OR_COEF_GAUSS = 2 };
 
 enum {
     OR_STATUS_PADE_SINGULAR = 1,
@@ -159,6 +168,13 @@ static int or_build_setup(const or_problem *pb, or_setup *s)
     if (pb->dim < 1 || pb->dim > OR_MAX_DIM) return -1;
     if (pb->f_deg < 0 || pb->f_deg > OR_MAX_DEG) return -1;
     if (!(pb->D >= 0.0)) return -1;
+    if (pb->coef_kind < OR_COEF_CONST || pb->coef_kind > OR_COEF_GAUSS) return -1;
+    if (pb->coef_kind == OR_COEF_GAUSS_OVER_T && !(pb->coef_param[6] > 0.0)) return -1;
+    /* A variable linear coefficient cannot be combined with a pulled-out
+     * constant potential: F's linear coefficient b_1 gamma + c is not b gamma. */
+    if (pb->coef_kind != OR_COEF_CONST && pb->strategy == OR_STRAT_A && pb->c_pot != 0.0 &&
+        ((pb->coef_mask >> 1) & 1u))
+        return -1;
     /* Terms: nonzero coefficients of F = f + c u (A) or f (B), ascending k. */
     for (int k = 0; k <= pb->f_deg; ++k) {
         double b = pb->f_coef[k];
@@ -271,6 +287,24 @@ static double or_u0(const or_problem *pb, const double *x)
     }
 }
 
+/* Variable-coefficient profile gamma(x, t) of the terms selected by the mask,
+ * c_k(x, t) = b_k gamma(x, t) (Sec. 1, Eq. nonlinear_new: f = sum_j c_j(x,t) u^j):
+ *   GAUSS_OVER_T  exp(-sum_i a_i (x_i - a_{3+i})^2) / (t + a6)   (Example 5 shape)
+ *   GAUSS         exp(-sum_i a_i (x_i - a_{3+i})^2)
+ * t is the PDE time at which the term acts. */
+static double or_gamma(const or_problem *pb, const double *x, double t)
+{
+    const double *a = pb->coef_param;
+    double r = 0.0;
+    for (int i = 0; i < pb->dim; ++i) {
+        double e = x[i] - a[3 + i];
+        r += a[i] * e * e;
+    }
+    double g = exp(-r);
+    if (pb->coef_kind == OR_COEF_GAUSS_OVER_T) g /= (t + a[6]);
+    return g;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One tree, walked recursively.                                            */
 /* ------------------------------------------------------------------------ */
@@ -366,8 +400,12 @@ static void or_visit(or_tree *T, const double *x, double tau, uint64_t id)
         T->pruned = 1;
         return;
     }
-    T->W *= factor;
     int k = s->arity[cat];
+    /* A variable coefficient acts where and when the particle splits: at the
+     * end y of this segment and at PDE time tau_child, the time left to its
+     * children (Sec. 2.1, Eq. probexp1: c_j(beta(S), t - S)). */
+    if (pb->coef_kind != OR_COEF_CONST && ((pb->coef_mask >> k) & 1u)) factor *= or_gamma(pb, y, tau_child);
+    T->W *= factor;
     for (int j = 0; j < k; ++j) {
         or_visit(T, y, tau_child, 16ull * id + (uint64_t)j + 1ull);
         if (T->pruned) return;

@@ -100,6 +100,29 @@ def eps_hierarchy_rk4(F_coef, c_pot, c0, t, K, steps=4000):
     return U
 
 
+def eps_hierarchy_rk4_t(coef_at, c_pot, c0, t, K, steps=4000):
+    """U_n(t) of u' = -c u + eps F(u, t), u(0) = c0, with time-dependent coefficients
+    F(u, t) = sum_k coef_at(t)[k] u^k, by RK4 on the order hierarchy."""
+    def rhs(U, s):
+        fs = series_poly_compose(coef_at(s), U, K + 1)
+        d = -c_pot * U
+        d[1:] += fs[:K]
+        return d
+
+    U = np.zeros(K + 1)
+    U[0] = c0
+    h = t / steps
+    s = 0.0
+    for _ in range(steps):
+        k1 = rhs(U, s)
+        k2 = rhs(U + 0.5 * h * k1, s + 0.5 * h)
+        k3 = rhs(U + 0.5 * h * k2, s + 0.5 * h)
+        k4 = rhs(U + h * k3, s + h)
+        U = U + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        s += h
+    return U
+
+
 def series_of_rational(num, den, nterms):
     """Taylor coefficients of num(e)/den(e) (den[0] != 0)."""
     a = np.zeros(nterms)
