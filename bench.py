@@ -588,6 +588,9 @@ def gpu_arm(args) -> int:
             "pdd_3d": dict(workload_bench(grt, local, "pdd_3d", 3), description=(
                 "3-D u_t = 0.1 Lap u + u - u^3, u0 = prod tanh(x_i - 2), 9 interior planes x 32^2 nodes of the "
                 "4x4x4 split of [0,4]^3, t = 1, 1e5 trees per point (9.2e8 trees), K = 12, [6/6]")),
+            "var_coef_2d": dict(workload_bench(grt, local, "var_coef_2d", 10), description=(
+                "Example 5: 2-D u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (variable coefficient), u0 = e^{-x^2/4}/sqrt(4 pi), "
+                "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, binary trees q = 2/3, K = 8, [4/4]")),
         }
     if not args.no_serving:
         line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,

@@ -76,6 +76,16 @@ extern "C" {
 #define GRT_U0_COS_PROD 2  /* p0 + p1 prod_i cos(p[2+i] x_i)                  */
 #define GRT_U0_TANH_PROD 3 /* p0 + p1 prod_i tanh(x_i - p[2+i])               */
 #define GRT_U0_LOGISTIC 4  /* p0 + p1 / (1 + exp(-(x_0 - p2) / p3))           */
+#define GRT_U0_GAUSS_AXES 5 /* p0 + p1 exp(-sum_i p_{2+i} (x_i - p_{5+i})^2)  */
+
+/* Variable coefficients c_k(x, t) = b_k gamma(x, t) of the terms selected by
+ * coef_mask (Sec. 1, Eq. nonlinear_new; Example 5 uses -e^{-x^2}/(t + 0.1) u^2).
+ * The split weight of a term k with bit k set is multiplied by gamma at the
+ * particle's position at the split and at the PDE time left to its children
+ * (Sec. 2.1, Eq. probexp1: c_j(beta(S), t - S)).  Parameters coef_param[0..7]: */
+#define GRT_COEF_CONST 0        /* gamma = 1 (coef_mask ignored)                           */
+#define GRT_COEF_GAUSS_OVER_T 1 /* exp(-sum_i p_i (x_i - p_{3+i})^2) / (t + p6), p6 > 0     */
+#define GRT_COEF_GAUSS 2        /* exp(-sum_i p_i (x_i - p_{3+i})^2)                        */
 
 /* Per-point status bits. */
 #define GRT_STATUS_PADE_SINGULAR 1  /* a Pade pivot was below 1e-14 of the largest matrix
@@ -98,6 +108,9 @@ typedef struct grt_problem {
     double q;                          /* B: leaf probability, 0 < q < 1                      */
     int32_t arity_law;                 /* GRT_ARITY_*                                         */
     int32_t precision;                 /* GRT_FP32 | GRT_FP64 (walk arithmetic)               */
+    int32_t coef_kind;                 /* GRT_COEF_*; Strategy A rejects a variable linear    */
+    double coef_param[8];              /*   term (mask bit 1) together with c_pot != 0        */
+    uint32_t coef_mask;                /* bit k: c_k(x, t) = b_k gamma(x, t), k <= f_deg      */
 } grt_problem;
 
 typedef struct grt_ctx grt_ctx;

@@ -14,7 +14,8 @@ Problem descriptions are plain dicts (see ``workloads.py``):
     f_coef     [b_0, ..., b_deg], f(u) = sum_k b_k u^k, deg <= 15
     u0         (kind, params): "const" (c,), "gauss" (c0, A, s, x0...),
                "cos_prod" (c0, A, w_0, w_1, w_2), "tanh_prod" (c0, A, s_0, s_1, s_2),
-               "logistic" (c0, A, x0, width)
+               "logistic" (c0, A, x0, width), "gauss_axes" (c0, A, w_0, w_1, w_2, m_0, m_1, m_2):
+               c0 + A exp(-sum_i w_i (x_i - m_i)^2)
     strategy   "A" (exponential clock, Sec. 2.1) or "B" (coin + uniform split, Sec. 2.2)
     lam, c_pot Strategy A clock rate and pulled-out potential
     q          Strategy B leaf probability
@@ -44,7 +45,7 @@ STATUS_PADE_POLE_NEAR = 2
 STATUS_SERIES_PARTIAL = 4
 STATUS_HIGH_PRUNE = 8
 
-_U0_KINDS = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4}
+_U0_KINDS = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5}
 _COEF_KINDS = {"const": 0, "gauss_over_t": 1, "gauss": 2}
 
 

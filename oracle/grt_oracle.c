@@ -95,7 +95,8 @@ typedef struct {
     uint32_t coef_mask; /* bit k: c_k(x, t) = b_k gamma(x, t) */
 } or_problem;
 
-enum { OR_U0_CONST = 0, OR_U0_GAUSS = 1, OR_U0_COS_PROD = 2, OR_U0_TANH_PROD = 3, OR_U0_LOGISTIC = 4 };
+enum { OR_U0_CONST = 0, OR_U0_GAUSS = 1, OR_U0_COS_PROD = 2, OR_U0_TANH_PROD = 3, OR_U0_LOGISTIC = 4,
+       OR_U0_GAUSS_AXES = 5 };
 enum { OR_STRAT_A = 0, OR_STRAT_B = 1 };
 enum { OR_COEF_CONST = 0, OR_COEF_GAUSS_OVER_T = 1, OR_COEF_GAUSS = 2 };
 
@@ -282,6 +283,14 @@ static double or_u0(const or_problem *pb, const double *x)
     }
     case OR_U0_LOGISTIC: /* a0 + a1 / (1 + exp(-(x_0 - a2) / a3)) */
         return a[0] + a[1] / (1.0 + exp(-(x[0] - a[2]) / a[3]));
+    case OR_U0_GAUSS_AXES: { /* a0 + a1 exp(-sum_i a[2+i] (x_i - a[5+i])^2) */
+        double r = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double e = x[i] - a[5 + i];
+            r += a[2 + i] * e * e;
+        }
+        return a[0] + a[1] * exp(-r);
+    }
     default:
         return NAN;
     }

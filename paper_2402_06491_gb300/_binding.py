@@ -23,7 +23,8 @@ OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP, EAGAIN = 0, -1, -2, -3, -4, -5, 
 STRATEGY = {"A": 0, "B": 1}
 ARITY_LAW = {"uniform": 0, "abs": 1}
 PRECISION = {"fp32": 0, "fp64": 1}
-U0_KIND = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4}
+U0_KIND = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5}
+COEF_KIND = {"const": 0, "gauss_over_t": 1, "gauss": 2}
 STATUS_PADE_SINGULAR, STATUS_PADE_POLE_NEAR, STATUS_SERIES_PARTIAL, STATUS_HIGH_PRUNE = 1, 2, 4, 8
 
 
@@ -47,6 +48,9 @@ class grt_problem(ctypes.Structure):
         ("q", ctypes.c_double),
         ("arity_law", ctypes.c_int32),
         ("precision", ctypes.c_int32),
+        ("coef_kind", ctypes.c_int32),
+        ("coef_param", ctypes.c_double * 8),
+        ("coef_mask", ctypes.c_uint32),
     ]
 
 
@@ -137,6 +141,12 @@ def problem_struct(pb: dict) -> grt_problem:
     s.q = float(pb.get("q", 0.5))
     s.arity_law = ARITY_LAW[pb.get("arity_law", "uniform")]
     s.precision = PRECISION[pb.get("precision", "fp32")]
+    if "coef" in pb:
+        kind, params, powers = pb["coef"]
+        s.coef_kind = COEF_KIND[kind]
+        for i, v in enumerate(params):
+            s.coef_param[i] = float(v)
+        s.coef_mask = sum(1 << int(k) for k in powers)
     return s
 
 

@@ -87,7 +87,7 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
   if (pb.f_deg < 0 || pb.f_deg > GRT_MAX_DEG) return why = "f_deg must be in [0, 15]", GRT_EINVAL;
   for (int k = 0; k <= pb.f_deg; ++k)
     if (!is_finite(pb.f_coef[k])) return why = "f_coef must be finite", GRT_EINVAL;
-  if (pb.u0_kind < GRT_U0_CONST || pb.u0_kind > GRT_U0_LOGISTIC) return why = "unknown u0_kind", GRT_EINVAL;
+  if (pb.u0_kind < GRT_U0_CONST || pb.u0_kind > GRT_U0_GAUSS_AXES) return why = "unknown u0_kind", GRT_EINVAL;
   for (int i = 0; i < 8; ++i)
     if (!is_finite(pb.u0_param[i])) return why = "u0_param must be finite", GRT_EINVAL;
   if (pb.u0_kind == GRT_U0_GAUSS && pb.u0_param[2] == 0.0) return why = "GAUSS width p2 must be nonzero", GRT_EINVAL;
@@ -101,6 +101,16 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
   if (A && !(is_finite(pb.lambda) && pb.lambda > 0.0)) return why = "Strategy A needs lambda > 0", GRT_EINVAL;
   if (A && !is_finite(pb.c_pot)) return why = "c_pot must be finite", GRT_EINVAL;
   if (!A && !(pb.q > 0.0 && pb.q < 1.0)) return why = "Strategy B needs 0 < q < 1", GRT_EINVAL;
+  if (pb.coef_kind < GRT_COEF_CONST || pb.coef_kind > GRT_COEF_GAUSS) return why = "unknown coef_kind", GRT_EINVAL;
+  const bool varcoef = pb.coef_kind != GRT_COEF_CONST;
+  if (varcoef) {
+    for (int i = 0; i < 8; ++i)
+      if (!is_finite(pb.coef_param[i])) return why = "coef_param must be finite", GRT_EINVAL;
+    if (pb.coef_kind == GRT_COEF_GAUSS_OVER_T && !(pb.coef_param[6] > 0.0))
+      return why = "GAUSS_OVER_T needs t0 = coef_param[6] > 0", GRT_EINVAL;
+    if (A && pb.c_pot != 0.0 && ((pb.coef_mask >> 1) & 1u))
+      return why = "a variable linear coefficient cannot be combined with c_pot != 0 (Strategy A)", GRT_EINVAL;
+  }
 
   // Terms: the nonzero coefficients of F = f + c u (A) or f (B), by ascending power.
   const int deg = (A && pb.f_deg < 1) ? 1 : pb.f_deg;
@@ -116,6 +126,19 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
     }
   }
   w.nterms = nt;
+  // variable coefficients: the categories (term indices) whose power is in the mask
+  w.coef_kind = pb.coef_kind;
+  w.coef_cat_mask = 0u;
+  for (int i = 0; i < 3; ++i) {
+    w.cwd[i] = varcoef ? -pb.coef_param[i] : 0.0;
+    w.cmd[i] = varcoef ? pb.coef_param[3 + i] : 0.0;
+    w.cwf[i] = (float)(w.cwd[i] * 1.4426950408889634);
+  }
+  w.ct0d = varcoef ? pb.coef_param[6] : 0.0;
+  w.ct0f = (float)w.ct0d;
+  if (varcoef)
+    for (int i = 0; i < nt; ++i)
+      if ((pb.coef_mask >> w.arity[i]) & 1u) w.coef_cat_mask |= 1u << i;
   for (int i = nt; i < grt::kMaxTerms; ++i) {
     w.arity[i] = 0;
     w.term_factor[i] = 0.0;
@@ -200,6 +223,12 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
     c[2] = a[2];
     c[3] = -1.0 / a[3];
     break;
+  case GRT_U0_GAUSS_AXES:
+    for (int i = 0; i < 3; ++i) {
+      c[2 + i] = -a[2 + i];
+      c[5 + i] = a[5 + i];
+    }
+    break;
   default:
     break;
   }
@@ -211,6 +240,8 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
   }
   if (pb.u0_kind == GRT_U0_GAUSS) w.u0f[2] = (float)(c[2] * log2e);
   if (pb.u0_kind == GRT_U0_LOGISTIC) w.u0f[3] = (float)(c[3] * log2e);
+  if (pb.u0_kind == GRT_U0_GAUSS_AXES)
+    for (int i = 2; i < 5; ++i) w.u0f[i] = (float)(c[i] * log2e);
   w.lam_minus_cf = (float)(w.lam_minus_c * log2e);
   return GRT_OK;
 }

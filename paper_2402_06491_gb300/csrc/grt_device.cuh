@@ -19,7 +19,8 @@ constexpr int kFinThreads = 128;  // threads of a finalize (binning) block
 constexpr int kBinChunk = 8192;   // tree records binned by one finalize block
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4 };
+enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4, kU0GaussAxes = 5 };
+enum : int { kCoefConst = 0, kCoefGaussOverT = 1, kCoefGauss = 2 };
 enum : int { kStratA = 0, kStratB = 1 };
 
 // Everything one walk launch needs, passed by value (constant bank).
@@ -41,6 +42,12 @@ struct WalkParams {
   double u0d[8];       // u0 constants (see make_u0_constants on the host)
   float u0f[8];
   float two_Df, inv_lambdaf, lam_minus_cf;
+  // variable coefficients c_k(x, t) = b_k gamma(x, t) (kCoef*): gamma multiplies the
+  // split factor of the categories in coef_cat_mask (bit = term index)
+  int coef_kind;
+  uint32_t coef_cat_mask;
+  double cwd[3], cmd[3], ct0d;  // -w_i, centre m_i, t0
+  float cwf[3], ct0f;           // -w_i log2 e, t0
   // Philox round keys: round r uses (k0 + r W0, k1 + r W1)
   uint32_t rk0[10], rk1[10];
   uint32_t point_base;
@@ -141,7 +148,7 @@ template <> __device__ __forceinline__ double pconst<double>(const WalkParams &p
 // The walk carries each particle's displacement D from its tree's root x_p, and
 // g is evaluated at x_p + D through these offsets, so an FP32 walk keeps full
 // relative accuracy near the initial data's centre, zeros and phases:
-//   GAUSS, TANH_PROD  base_i = x_p,i - centre_i
+//   GAUSS, TANH_PROD, GAUSS_AXES  base_i = x_p,i - centre_i
 //   LOGISTIC          base_0 = x_p,0 - centre
 //   COS_PROD          base_i = omega_i x_p,i reduced to [-pi, pi]
 template <typename Real, int DIM>
@@ -153,6 +160,7 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
     case kU0Gauss: b = xp[i] - p.u0d[3 + i]; break;
     case kU0TanhProd: b = xp[i] - p.u0d[2 + i]; break;
     case kU0Logistic: b = i == 0 ? xp[0] - p.u0d[2] : 0.0; break;
+    case kU0GaussAxes: b = xp[i] - p.u0d[5 + i]; break;
     case kU0CosProd: b = remainder(p.u0d[2 + i] * xp[i], 6.283185307179586476925286766559); break;
     default: break;
     }
@@ -166,6 +174,7 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
 //   COS_PROD  c0, A, w0, w1, w2
 //   TANH_PROD c0, A, s0, s1, s2
 //   LOGISTIC  c0, A, x0, -1/width
+//   GAUSS_AXES c0, A, -w0, -w1, -w2, m0, m1, m2
 template <typename Real, int DIM>
 __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&base)[DIM], const Real (&D)[DIM]) {
   using M = Math<Real>;
@@ -194,9 +203,48 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&b
   }
   case kU0Logistic:
     return c0 + A / (Real(1) + Node<Real>::exp_scaled((base[0] + D[0]) * pconst<Real>(p, 3)));
+  case kU0GaussAxes: {
+    Real r = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const Real e = base[i] + D[i];
+      r += pconst<Real>(p, 2 + i) * e * e;
+    }
+    return c0 + A * Node<Real>::exp_scaled(r);
+  }
   default:
     return c0;
   }
+}
+
+// Variable-coefficient profile gamma at the root's point xp plus displacement y,
+// at PDE time t (kinds as GRT_COEF_*):
+//   GAUSS_OVER_T  exp(-sum_i w_i (x_i - m_i)^2) / (t + t0)
+//   GAUSS         exp(-sum_i w_i (x_i - m_i)^2)
+// The offset x_p - m is formed in FP64 and the displacement added in the walk's
+// precision, as for the initial data.
+template <typename Real, int DIM>
+__device__ __forceinline__ Real coef_gamma(const WalkParams &p, const double *__restrict__ xp, const Real (&y)[DIM],
+                                           Real t) {
+  Real r = Real(0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    const Real e = (Real)(xp[i] - p.cmd[i]) + y[i];
+    if constexpr (sizeof(Real) == 4) {
+      r += p.cwf[i] * e * e;
+    } else {
+      r += p.cwd[i] * e * e;
+    }
+  }
+  Real g = Node<Real>::exp_scaled(r);
+  if (p.coef_kind == kCoefGaussOverT) {
+    if constexpr (sizeof(Real) == 4) {
+      g = g / (t + p.ct0f);
+    } else {
+      g = g / (t + p.ct0d);
+    }
+  }
+  return g;
 }
 
 template <typename Real> struct Scalars;
@@ -238,13 +286,18 @@ template <typename Real, int DIM> struct NodeOut {
 //   Strategy A: lifetime S = -ln(U)/lambda; S >= tau: leaf with weight
 //     e^{(lambda-c) tau} g(x + sqrt(2 D tau) n); else split at S with weight
 //     e^{(lambda-c) S} b_k / (lambda p_k), children at remaining time tau - S.
+// A variable coefficient (coef_kind != 0, the term's bit in coef_cat_mask)
+// multiplies the split factor by gamma at the split position and at the PDE
+// time left to the children (Sec. 2.1, Eq. probexp1: c_j(beta(S), t - S)).
 // `s_factor`, `s_thr` and the caller's arity table are block-shared copies of the tables;
-// x is the displacement from the tree's root and `base` the root's shifted origin.
+// x is the displacement from the tree's root, `base` the root's shifted origin
+// and xp the root's coordinates (read only by a variable coefficient).
 template <typename Real, int DIM, int STRAT>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
                                           const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
-                                          const Real (&x)[DIM], Real tau, uint32_t id_lo, uint32_t id_hi,
-                                          uint32_t tree, uint32_t point, NodeOut<Real, DIM> &o) {
+                                          const double *__restrict__ xp, const Real (&x)[DIM], Real tau,
+                                          uint32_t id_lo, uint32_t id_hi, uint32_t tree, uint32_t point,
+                                          NodeOut<Real, DIM> &o) {
   using M = Math<Real>;
   const uint4 w = philox4x32_10(make_uint4(id_lo, id_hi, tree, point), p.rk0, p.rk1);
   // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
@@ -299,6 +352,8 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
       const Real lmc = Scalars<Real>::lam_minus_c(p);
       o.factor = (lmc == Real(0)) ? tf : F::exp_scaled(lmc * S) * tf;
     }
+    if (p.coef_kind != kCoefConst && ((p.coef_cat_mask >> o.cat) & 1u))
+      o.factor *= coef_gamma<Real, DIM>(p, xp, o.y, o.tau_c);
   }
 }
 

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
   const unsigned lt_mask = (1u << lane) - 1u;
 
   // warp-uniform: the chunk trees are handed out from
-  uint32_t c_next = 0, c_end = 0, c_point = 0, c_first = 0;
+  uint32_t c_next = 0, c_end = 0, c_point = 0, c_first = 0, c_pt = 0;
   uint64_t c_rec = 0;
   Real c_t = Real(0), c_base[DIM];
 #pragma unroll
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
 
   // lane: its tree and the tree's point
   bool active = false;
-  uint32_t tree = 0, point = 0;
+  uint32_t tree = 0, point = 0, pidx = 0;
   uint64_t rec = 0;
   Real base[DIM];
   // lane: the current node (position, remaining time, label) and the running tree
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
           c_first = p.tree_first ? __ldg(p.tree_first + pt) : 0u;
           c_rec = __ldg(p.tree_prefix + pt);
           c_t = (Real)__ldg(p.t + pt);
+          c_pt = (uint32_t)pt;
           double xp[DIM];
 #pragma unroll
           for (int i = 0; i < DIM; ++i) xp[i] = __ldg(p.x + (size_t)pt * DIM + i);
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
         if (((idle >> lane) & 1u) && rank < avail) {
           tree = c_first + c_next + rank;  // the tree's index in its point's stream
           point = c_point;
+          pidx = c_pt;
           rec = c_rec + c_next + rank;
 #pragma unroll
           for (int i = 0; i < DIM; ++i) {
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
     // pending sibling from the stack (up), or the tree is done.
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, id_lo, id_hi, tree, point, o);
+    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, p.x + (size_t)pidx * DIM, x, tau, id_lo, id_hi, tree,
+                                point, o);
     W *= o.factor;
     const bool split = o.cat >= 0;
     Ne += split ? 1 : 0;
@@ -279,7 +282,8 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
   for (;;) {
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, x, tau, (uint32_t)id, (uint32_t)(id >> 32), tree, point, o);
+    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, xin, x, tau, (uint32_t)id, (uint32_t)(id >> 32), tree,
+                                point, o);
     h = (h ^ (uint64_t)(o.cat + 1)) * 0x100000001B3ull;
     W *= o.factor;
     bool descend = false;

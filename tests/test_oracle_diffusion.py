@@ -109,3 +109,23 @@ def test_first_order_checker_against_brute_quadrature():
 
     brute = b * integrate.quad(integrand, 0.0, t, epsrel=1e-8)[0]
     assert abs(first_order_gauss_1d([x], t, D, A, s, b)[0] - brute) < 1e-8
+
+
+def test_a0_axis_gaussian_2d(oracle_mod):
+    # g = c0 + A exp(-sum_i w_i (x_i - m_i)^2): each axis convolves separately,
+    # (P_t g)(x) = c0 + A prod_i (1 + 4 w_i D t)^{-1/2} exp(-w_i (x_i - m_i)^2 / (1 + 4 w_i D t));
+    # w_1 = 0 is the Example 5 initial data (a function of x_0 alone)
+    pb = workloads.problem_var_coef_2d()
+    c0, A, w0, w1, _, m0, m1, _ = pb["u0"][1]
+    x = np.array([[0.0, 0.0], [1.5, -2.0], [-2.5, 0.7]])
+    t, D = 0.5, pb["D"]
+    pb0 = dict(pb)
+    pb0.pop("coef")
+    a, se = _solve(oracle_mod, pb0, x, t, 200_000, 4)
+    expect = np.full(len(x), c0)
+    g = np.ones(len(x)) * A
+    for i, (w, m) in enumerate(((w0, m0), (w1, m1))):
+        s = 1.0 + 4.0 * w * D * t
+        g *= np.exp(-w * (x[:, i] - m) ** 2 / s) / math.sqrt(s)
+    expect = expect + g
+    assert np.all(np.abs(a[:, 0] - expect) <= 4.5 * se[:, 0]), (a[:, 0], expect, se[:, 0])

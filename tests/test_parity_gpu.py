@@ -103,6 +103,13 @@ PER_TREE = [
                             strategy="B", q=0.7, arity_law="uniform", precision="fp64"), [0.4], 0.8, 10),
     ("const-term B fp32", dict(dim=2, D=0.3, f_coef=[0.5, 0.0, 1.0], u0=("cos_prod", (0.2, 1.0, 0.5, 1.5)),
                                strategy="B", q=0.55, arity_law="abs", precision="fp32"), [0.1, 0.2], 0.9, 10),
+    ("var-coef ex5 B fp32", workloads.problem_var_coef_2d(), [0.4, -1.1], 0.5, 8),
+    ("var-coef ex5 B fp64", workloads.problem_var_coef_2d(precision="fp64"), [-0.9, 0.3], 0.5, 8),
+    ("var-coef ex5 A fp64", workloads.problem_var_coef_2d("A", "fp64"), [1.3, 0.0], 0.5, 8),
+    ("var-coef 3d masked B fp32", dict(dim=3, D=0.4, f_coef=[0.0, 0.5, 1.0, -0.6],
+                                       u0=("gauss_axes", (0.1, 0.8, 0.3, 0.5, 0.2, 0.1, -0.2, 0.3)),
+                                       coef=("gauss", (0.6, 0.2, 0.9, 0.3, 0.0, -0.4), [1, 3]), strategy="B", q=0.6,
+                                       arity_law="uniform", precision="fp32"), [0.2, 0.4, -0.1], 0.7, 10),
 ]
 
 
@@ -128,6 +135,26 @@ def test_per_tree_records(grt, name, pb, x, t, K):
         assert np.all(dw <= 3e-5 * aw + 1e-6 * aw.max()), np.max(dw / np.maximum(aw, 1e-300))
         rel_ok = dw <= 3e-5 * aw
         assert rel_ok[aw > 1e-30].mean() > 0.99, rel_ok.mean()
+
+
+def test_unit_profile_leaves_gpu_trees_unchanged(grt):
+    # gamma = exp(0) = 1 on every term: the records must equal the constant-coefficient walk bit for bit
+    base = dict(dim=2, D=0.5, f_coef=[0.2, -0.5, 1.0, 0.3], u0=("gauss", (0.1, 1.0, 0.8, 0.2, -0.3)), strategy="B",
+                q=0.55, arity_law="abs", precision="fp32")
+    unit = dict(base, coef=("gauss", (0, 0, 0, 0.4, 0.5, 0), [0, 1, 2, 3]))
+    out = []
+    for pb in (base, unit):
+        ctx = grt.grt_create(pb, 0)
+        out.append(grt.grt_trees(ctx, [0.3, -0.2], 0.8, 3, 0, 5000, 10, 5))
+        ctx.close()
+    for k in ("order", "nodes", "hash", "w"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_variable_coefficient_point_solve(grt):
+    wl = workloads.subsample(workloads.workload_var_coef_2d(), 24, ntrees=3000)
+    g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
+    _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"])
 
 
 def test_strategy_a_fp32_topology_mismatches_are_rare(grt):
@@ -281,3 +308,12 @@ def test_full_size_sin_2d_sampled_points(grt):
                          wl["M"], wl["seed"], point_base=i)
         gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
         _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], L=wl["L"], M=wl["M"])
+
+
+def test_invalid_coefficient_profiles_rejected(grt):
+    bad = [dict(workloads.problem_var_coef_2d(), coef=("gauss_over_t", (1, 0, 0, 0, 0, 0, 0.0), [2])),
+           dict(workloads.problem_var_coef_2d("A"), f_coef=[0.0, 0.5, -1.0], c_pot=1.0,
+                coef=("gauss", (1, 0, 0, 0, 0, 0), [1, 2]))]
+    for pb in bad:
+        with pytest.raises(grt.GrtError):
+            grt.grt_create(pb, 0)

@@ -16,6 +16,8 @@ probabilistic-domain-decomposition set-up (Sec. 2.4 Examples 1-3, Sec. 3):
     sin_2d     u_t = 0.5 Lap u + sin(u) (sin as its degree-9 Taylor polynomial)
     uneven_2d  u_t = Lap u + u^2 on PDD interface points, uneven tree budgets
     pdd_3d     u_t = 0.1 Lap u + u - u^3 on the 9 interior planes of a 4x4x4 split
+    var_coef_2d  u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (Sec. 3 Example 5: a variable
+               coefficient on the nonlinear term), u0 = e^{-x^2/4}/sqrt(4 pi), t = 0.5
 """
 from __future__ import annotations
 
@@ -72,6 +74,14 @@ def problem_uneven_2d() -> dict:
 def problem_pdd_3d() -> dict:
     return dict(dim=3, D=0.1, f_coef=[0.0, 1.0, 0.0, -1.0], u0=("tanh_prod", (0.0, 1.0, 2.0, 2.0, 2.0)),
                 strategy="B", lam=1.0, c_pot=0.0, q=2.0 / 3.0, arity_law="uniform", precision="fp32")
+
+
+def problem_var_coef_2d(strategy: str = "B", precision: str = "fp32") -> dict:
+    """Example 5: c_2(x, t) = -e^{-x_0^2} / (t + 0.1), binary trees, u0 a function of x_0 alone."""
+    return dict(dim=2, D=1.0, f_coef=[0.0, 0.0, -1.0], u0=("gauss_axes", (0.0, 1.0 / math.sqrt(4.0 * math.pi),
+                                                                       0.25, 0.0, 0.0, 0.0, 0.0, 0.0)),
+                coef=("gauss_over_t", (1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.1), [2]), strategy=strategy, lam=1.0,
+                c_pot=0.0, q=2.0 / 3.0, arity_law="uniform", precision=precision)
 
 
 def workload_kpp_1d() -> dict:
@@ -138,11 +148,21 @@ def workload_pdd_3d() -> dict:
                 K=12, L=6, M=6, seed=0)
 
 
+def workload_var_coef_2d() -> dict:
+    g = np.linspace(-3.0, 3.0, 16)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x = np.stack([X.ravel(), Y.ravel()], axis=1)
+    n = x.shape[0]
+    return dict(name="var_coef_2d", problem=problem_var_coef_2d(), x=x, t=np.full(n, 0.5),
+                ntrees=np.full(n, 100_000, np.uint64), K=8, L=4, M=4, seed=0)
+
+
 WORKLOADS = {
     "kpp_1d": workload_kpp_1d,
     "sin_2d": workload_sin_2d,
     "uneven_2d": workload_uneven_2d,
     "pdd_3d": workload_pdd_3d,
+    "var_coef_2d": workload_var_coef_2d,
 }
 
 
