@@ -54,6 +54,20 @@ class grt_problem(ctypes.Structure):
     ]
 
 
+class grt_pdd_grid(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("sub", ctypes.c_int32 * 3),
+        ("cells", ctypes.c_int32 * 3),
+        ("nodes", ctypes.c_int32 * 3),
+        ("t_nodes", ctypes.c_int32),
+        ("T", ctypes.c_double),
+        ("nsteps", ctypes.c_int32),
+    ]
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _lib = None
@@ -94,6 +108,9 @@ def _load():
         "grt_submit": ([_vp, _vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, u64p], i32),
         "grt_poll": ([_vp, u64, i32, f64p, f64p, f64p, i32p, f64p], i32),
         "grt_server_stats": ([_vp, u64p, u64p, u64p, u64p, u64p, u64p], i32),
+        "grt_spline_grid": ([_vp, i32, i32p, f64p, f64p, i32p, f64p, i64, _vp, _vp, _vp], i32),
+        "grt_pdd_points": ([_P(grt_pdd_grid), i64, f64p, f64p, _P(ctypes.c_int64)], i32),
+        "grt_pdd_solve": ([_vp, _P(grt_pdd_grid), _vp, _vp, i32p, _vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -491,9 +508,77 @@ def grt_server_stats(server: Server) -> dict:
     return {k: int(v.value) for k, v in zip(keys, vals)}
 
 
+# ---------------------------------------------------------------------------
+# probabilistic domain decomposition (Sec. 3)
+# ---------------------------------------------------------------------------
+def pdd_grid_struct(g: dict) -> grt_pdd_grid:
+    """Marshal a PDD grid dict (dim, lo, hi, sub, cells, nodes, t_nodes, T, nsteps) into the C struct."""
+    s = grt_pdd_grid()
+    d = int(g["dim"])
+    s.dim = d
+    for a in range(d):
+        s.lo[a] = float(g["lo"][a])
+        s.hi[a] = float(g["hi"][a])
+        s.sub[a] = int(g["sub"][a])
+        s.cells[a] = int(g["cells"][a])
+        s.nodes[a] = int(g["nodes"][a]) if "nodes" in g else 0
+    s.t_nodes = int(g["t_nodes"])
+    s.T = float(g["T"])
+    s.nsteps = int(g["nsteps"])
+    return s
+
+
+def grt_pdd_points(grid: dict):
+    """The probabilistic nodal points (x [n][dim], t [n]) of a PDD grid, in the order grt_pdd_solve reads."""
+    lib = _load()
+    gs = pdd_grid_struct(grid)
+    n = ctypes.c_int64(0)
+    _check(lib.grt_pdd_points(ctypes.byref(gs), 0, None, None, ctypes.byref(n)))
+    x = np.zeros((n.value, gs.dim), np.float64)
+    t = np.zeros(n.value, np.float64)
+    _check(lib.grt_pdd_points(ctypes.byref(gs), n.value, _ptr(x, ctypes.c_double), _ptr(t, ctypes.c_double),
+                              ctypes.byref(n)))
+    return x, t
+
+
+def grt_pdd_solve(ctx: Context, grid: dict, u_nodes, u_out, stream=None, info: bool = True):
+    """PDD solution at T on the global grid into the device buffer u_out (N[0] x ... row-major).
+    u_nodes: device values at grt_pdd_points.  Returns [max CG iterations, capped steps] when info."""
+    lib = _load()
+    gs = pdd_grid_struct(grid)
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    inf = np.zeros(2, np.int32)
+    rc = lib.grt_pdd_solve(ctx.handle, ctypes.byref(gs), _devptr(u_nodes), _devptr(u_out),
+                           _ptr(inf, ctypes.c_int32) if info else None, sh)
+    _check(rc, ctx.handle)
+    return [int(v) for v in inf] if info else None
+
+
+def grt_spline_grid(ctx: Context, n_nodes, lo, hi, targets, values, out, batch: int = 1, stream=None) -> None:
+    """Tensor-product not-a-knot spline on a uniform grid: values (device, [batch][n_nodes...]) at the grid
+    of target coordinates (a list of 1-D host arrays, one per axis) into out (device, [batch][n_targets...])."""
+    lib = _load()
+    nd = len(n_nodes)
+    nn = np.ascontiguousarray(n_nodes, np.int32)
+    lo_ = np.ascontiguousarray(lo, np.float64)
+    hi_ = np.ascontiguousarray(hi, np.float64)
+    nt = np.ascontiguousarray([len(v) for v in targets], np.int32)
+    tg = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in targets]))
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.grt_spline_grid(ctx.handle, nd, _ptr(nn, ctypes.c_int32), _ptr(lo_, ctypes.c_double),
+                             _ptr(hi_, ctypes.c_double), _ptr(nt, ctypes.c_int32), _ptr(tg, ctypes.c_double),
+                             int(batch), _devptr(values), _devptr(out), sh)
+    _check(rc, ctx.handle)
+
+
 EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
             "grt_plan_set_config", "grt_plan_get_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
             "grt_pade", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
-            "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats"]
+            "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",
+            "grt_pdd_points", "grt_pdd_solve"]

@@ -440,6 +440,7 @@ void grt_destroy(grt_ctx *ctx) {
   ctx->dcoef.release();
   ctx->dse.release();
   ctx->dstatus.release();
+  ctx->pdd_scratch.release();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -51,6 +51,7 @@ struct grt_ctx {
   cudaStream_t stream = nullptr;
   grt_plan *solve_plan = nullptr;
   grt::DevBuf dx, dt, du, dcoef, dse, dstatus;
+  grt::DevBuf pdd_scratch;  // spline weights, staging, plane data and subdomain vectors of the PDD stages
   int set_error(int code, const std::string &msg) {
     err = msg;
     return code;

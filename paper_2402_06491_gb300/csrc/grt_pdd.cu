@@ -1,0 +1,720 @@
+// grt_pdd.cu -- the probabilistic-domain-decomposition stages after the point
+// solve (Sec. 3): a tensor-product not-a-knot cubic spline of the interface
+// values and independent Crank-Nicolson solves of the subdomains.
+//
+// GPU layout:
+//   * spline: a weights kernel (one thread per nodal column: the not-a-knot
+//     system of a unit data vector by elimination, then the cubic at every
+//     target) and an axis-contraction kernel applied once per axis, FP64;
+//   * local solver: one thread block per subdomain runs every time step with
+//     its vectors in global memory (L2-resident: a few MB in all) and a
+//     conjugate-gradient solve per step; the subdomains share nothing, which
+//     is the decoupling the method is built on (Sec. 3, "Local solver").
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grt.h"
+#include "grt_host.h"
+
+namespace grt {
+
+// ---------------------------------------------------------------------------
+// spline weights: W[t][j] = s_j(target t), s_j the not-a-knot cubic spline of
+// the unit vector e_j on n uniform nodes lo + i hn (Sec. 3, Interpolation).
+// With uniform spacing the second derivatives M_i satisfy
+//   M_{i-1} + 4 M_i + M_{i+1} = r_i = 6 (y_{i+1} - 2 y_i + y_{i-1}) / hn^2,  i = 1..n-2,
+// and not-a-knot (s''' continuous at x_1, x_{n-2}) gives M_0 = 2 M_1 - M_2 and
+// M_{n-1} = 2 M_{n-2} - M_{n-3}; substituted into rows 1 and n-2 these give
+// M_1 = r_1 / 6 and M_{n-2} = r_{n-2} / 6, leaving a tridiagonal system for
+// M_2..M_{n-3} (Thomas elimination).  On [x_i, x_{i+1}], A = (x_{i+1} - x)/hn,
+// B = 1 - A: s = A y_i + B y_{i+1} + ((A^3 - A) M_i + (B^3 - B) M_{i+1}) hn^2 / 6.
+// ---------------------------------------------------------------------------
+__global__ void spline_weights_kernel(int n, double lo, double hn, int m, const double *__restrict__ targets,
+                                      double *__restrict__ W) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double M[GRT_SPLINE_MAX_NODES], cp[GRT_SPLINE_MAX_NODES];
+  const double s6 = 6.0 / (hn * hn);
+  auto r_at = [&](int i) -> double {  // 6 (y_{i+1} - 2 y_i + y_{i-1}) / hn^2 for y = e_j
+    double v = 0.0;
+    if (i + 1 == j || i - 1 == j) v += 1.0;
+    if (i == j) v -= 2.0;
+    return v * s6;
+  };
+  M[1] = r_at(1) / 6.0;
+  M[n - 2] = r_at(n - 2) / 6.0;
+  // M_2..M_{n-3}: diagonal 4, off-diagonals 1 (forward sweep, back substitution)
+  const int first = 2, last = n - 3;
+  for (int i = first; i <= last; ++i) {
+    double rhs = r_at(i);
+    if (i == first) rhs -= M[1];
+    if (i == last) rhs -= M[n - 2];
+    const double denom = (i == first) ? 4.0 : 4.0 - cp[i - 1];
+    cp[i] = 1.0 / denom;
+    M[i] = (i == first) ? rhs / denom : (rhs - M[i - 1]) / denom;
+  }
+  for (int i = last - 1; i >= first; --i) M[i] -= cp[i] * M[i + 1];
+  M[0] = 2.0 * M[1] - M[2];
+  M[n - 1] = 2.0 * M[n - 2] - M[n - 3];
+  const double hh6 = hn * hn / 6.0;
+  for (int t = 0; t < m; ++t) {
+    const double xt = targets[t];
+    int i = (int)floor((xt - lo) / hn);
+    i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+    const double A = (lo + (double)(i + 1) * hn - xt) / hn, B = 1.0 - A;
+    double v = 0.0;
+    if (i == j) v += A;
+    if (i + 1 == j) v += B;
+    v += ((A * A * A - A) * M[i] + (B * B * B - B) * M[i + 1]) * hh6;
+    W[(size_t)t * n + j] = v;
+  }
+}
+
+// out[o][i][r] = sum_j W[i][j] in[o][j][r]: one axis of the tensor-product spline.
+__global__ void axis_apply_kernel(const double *__restrict__ W, int m, int n, const double *__restrict__ in,
+                                  double *__restrict__ out, long long outer, long long inner) {
+  const long long total = outer * (long long)m * inner;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % inner;
+    const long long oi = e / inner;
+    const int i = (int)(oi % m);
+    const long long o = oi / m;
+    const double *src = in + (o * n) * inner + r;
+    const double *w = W + (size_t)i * n;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(w[j], src[(long long)j * inner], acc);
+    out[e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PDD device description
+// ---------------------------------------------------------------------------
+struct PddDev {
+  int dim;
+  int N[3], cells[3], sub[3], m[3];
+  double lo[3], h[3], inv_h2[3];
+  int nsteps;
+  double dt, alpha;
+  const double *B[3];        // per axis: [sub+1][nsteps][plane FD nodes] (levels t_1..t_N)
+  long long plane_elems[3];  // FD nodes of one axis-a plane
+  int f_deg;
+  double f_coef[GRT_MAX_DEG + 1];
+  uint32_t coef_pow_mask;    // powers k whose coefficient is b_k gamma(x, t)
+  double *work;              // [nsub][6][mloc]
+  int mloc;
+  double tol2;
+  int max_iter;
+  int *info;                 // [0] largest CG iteration count, [1] steps at the cap
+  double *u_out;
+};
+
+// initial data at a point (FP64, the walk's own formulas with zero displacement)
+template <int DIM> __device__ __forceinline__ double u0_at(const WalkParams &p, const double (&x)[3]) {
+  double base[DIM], zero[DIM];
+  initial_data_base<double, DIM>(p, x, base);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) zero[i] = 0.0;
+  return initial_data<double, DIM>(p, base, zero);
+}
+
+// f(u, x, t) = sum_k c_k(x, t) u^k (Horner on the constant and on the gamma-scaled powers)
+template <int DIM>
+__device__ __forceinline__ double f_at(const WalkParams &p, const PddDev &q, const double (&x)[3], double t,
+                                       double u) {
+  double fc = 0.0, fg = 0.0;
+  const bool var = p.coef_kind != kCoefConst;
+  for (int k = q.f_deg; k >= 0; --k) {
+    const bool vk = var && ((q.coef_pow_mask >> k) & 1u);
+    fc = fc * u + (vk ? 0.0 : q.f_coef[k]);
+    fg = fg * u + (vk ? q.f_coef[k] : 0.0);
+  }
+  if (!var) return fc;
+  double zero[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) zero[i] = 0.0;
+  return fc + coef_gamma<double, DIM>(p, x, zero, t) * fg;
+}
+
+// Dirichlet value of the ring node next to interior node gi (global indices)
+// across face `side` of axis a, at level n (0: initial data).
+template <int DIM>
+__device__ __forceinline__ double ring_value(const WalkParams &p, const PddDev &q, const int (&s)[3],
+                                             const int (&gi)[3], int a, int side, int n) {
+  int g[3] = {gi[0], gi[1], gi[2]};
+  const int k = s[a] + side;
+  g[a] = k * q.cells[a];
+  if (n == 0) {
+    double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) x[b] = q.lo[b] + (double)g[b] * q.h[b];
+    return u0_at<DIM>(p, x);
+  }
+  long long off = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b)
+    if (b != a) off = off * q.N[b] + g[b];
+  return q.B[a][((long long)k * q.nsteps + (n - 1)) * q.plane_elems[a] + off];
+}
+
+template <int NT> __device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // red[] free from the previous use
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += red[i];  // fixed order: deterministic
+  return s;
+}
+
+template <int DIM> __device__ __forceinline__ void local_index(const PddDev &q, int l, int (&i)[3]) {
+  i[0] = i[1] = i[2] = 0;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) {
+    i[a] = l % q.m[a];
+    l /= q.m[a];
+  }
+}
+
+// (A v)_l = v_l - alpha Lap_h^0 v at local node l (zero ring)
+template <int DIM>
+__device__ __forceinline__ double apply_A(const PddDev &q, const double *__restrict__ v, int l, const int (&i)[3],
+                                          const int (&stride)[3]) {
+  const double c = v[l];
+  double lap = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const double left = i[a] > 0 ? v[l - stride[a]] : 0.0;
+    const double right = i[a] < q.m[a] - 1 ? v[l + stride[a]] : 0.0;
+    lap += (left + right - 2.0 * c) * q.inv_h2[a];
+  }
+  return c - q.alpha * lap;
+}
+
+// One block per subdomain: every Crank-Nicolson step, CG per step.
+template <int DIM, int NT>
+__global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, const PddDev q) {
+  __shared__ double red[NT / 32];
+  const int sid = blockIdx.x;
+  int s[3] = {0, 0, 0};
+  {
+    int r = sid;
+#pragma unroll
+    for (int a = DIM - 1; a >= 0; --a) {
+      s[a] = r % q.sub[a];
+      r /= q.sub[a];
+    }
+  }
+  const int mloc = q.mloc;
+  double *u = q.work + (size_t)sid * 6 * mloc;
+  double *up = u + mloc, *x = up + mloc, *r = x + mloc, *pv = r + mloc, *Ap = pv + mloc;
+  int stride[3] = {1, 1, 1};
+#pragma unroll
+  for (int a = DIM - 2; a >= 0; --a) stride[a] = stride[a + 1] * q.m[a + 1];
+
+  auto node = [&](int l, int (&i)[3], int (&gi)[3], double (&xc)[3]) {
+    local_index<DIM>(q, l, i);
+    xc[0] = xc[1] = xc[2] = 0.0;
+    gi[0] = gi[1] = gi[2] = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      gi[a] = s[a] * q.cells[a] + 1 + i[a];
+      xc[a] = q.lo[a] + (double)gi[a] * q.h[a];
+    }
+  };
+
+  for (int l = threadIdx.x; l < mloc; l += NT) {
+    int i[3], gi[3];
+    double xc[3];
+    node(l, i, gi, xc);
+    u[l] = u0_at<DIM>(p, xc);
+    up[l] = u[l];
+  }
+  __syncthreads();
+
+  int it_max = 0, fails = 0;
+  for (int n = 0; n < q.nsteps; ++n) {
+    // initial guess: the linear extrapolation 2 u^n - u^{n-1} (u^0 on the first step)
+    for (int l = threadIdx.x; l < mloc; l += NT) x[l] = n == 0 ? u[l] : 2.0 * u[l] - up[l];
+    __syncthreads();
+    // right-hand side and the first residual r = b - A x
+    const double th = ((double)n + 0.5) * q.dt;
+    double bb = 0.0, rr0 = 0.0;
+    for (int l = threadIdx.x; l < mloc; l += NT) {
+      int i[3], gi[3];
+      double xc[3];
+      node(l, i, gi, xc);
+      const double c = u[l];
+      double lap = 0.0, ring1 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double left = i[a] > 0 ? u[l - stride[a]] : ring_value<DIM>(p, q, s, gi, a, 0, n);
+        const double right = i[a] < q.m[a] - 1 ? u[l + stride[a]] : ring_value<DIM>(p, q, s, gi, a, 1, n);
+        lap += (left + right - 2.0 * c) * q.inv_h2[a];
+        double rn = 0.0;
+        if (i[a] == 0) rn += ring_value<DIM>(p, q, s, gi, a, 0, n + 1);
+        if (i[a] == q.m[a] - 1) rn += ring_value<DIM>(p, q, s, gi, a, 1, n + 1);
+        ring1 += rn * q.inv_h2[a];
+      }
+      const double ustar = n == 0 ? c : 1.5 * c - 0.5 * up[l];
+      const double b = c + q.alpha * lap + q.alpha * ring1 + q.dt * f_at<DIM>(p, q, xc, th, ustar);
+      const double res = b - apply_A<DIM>(q, x, l, i, stride);
+      r[l] = res;
+      pv[l] = res;
+      bb += b * b;
+      rr0 += res * res;
+    }
+    bb = block_sum<NT>(bb, red);
+    double rr = block_sum<NT>(rr0, red);
+    const double stop = q.tol2 * bb;
+    int it = 0;
+    while (rr > stop && it < q.max_iter) {
+      double pap = 0.0;
+      for (int l = threadIdx.x; l < mloc; l += NT) {
+        int i[3];
+        local_index<DIM>(q, l, i);
+        const double a = apply_A<DIM>(q, pv, l, i, stride);
+        Ap[l] = a;
+        pap += pv[l] * a;
+      }
+      pap = block_sum<NT>(pap, red);
+      const double step = rr / pap;
+      double rn = 0.0;
+      for (int l = threadIdx.x; l < mloc; l += NT) {
+        x[l] = fma(step, pv[l], x[l]);
+        const double v = fma(-step, Ap[l], r[l]);
+        r[l] = v;
+        rn += v * v;
+      }
+      rn = block_sum<NT>(rn, red);
+      const double beta = rn / rr;
+      for (int l = threadIdx.x; l < mloc; l += NT) pv[l] = fma(beta, pv[l], r[l]);
+      __syncthreads();
+      rr = rn;
+      ++it;
+    }
+    it_max = it > it_max ? it : it_max;
+    if (rr > stop) ++fails;
+    // rotate: u^{n-1} <- u^n, u^n <- x
+    double *t0 = up;
+    up = u;
+    u = x;
+    x = t0;
+    __syncthreads();
+  }
+  for (int l = threadIdx.x; l < mloc; l += NT) {
+    int i[3], gi[3];
+    double xc[3];
+    node(l, i, gi, xc);
+    long long off = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) off = off * q.N[a] + gi[a];
+    q.u_out[off] = u[l];
+  }
+  if (threadIdx.x == 0) {
+    atomicMax(q.info, it_max);
+    if (fails) atomicAdd(q.info + 1, fails);
+  }
+}
+
+// Plane nodes of the output: the spline at T, the lowest axis's plane on edges.
+template <int DIM> __global__ void pdd_planes_kernel(const PddDev q) {
+  long long total = 1;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) total *= q.N[a];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int g[3] = {0, 0, 0};
+    long long r = e;
+#pragma unroll
+    for (int a = DIM - 1; a >= 0; --a) {
+      g[a] = (int)(r % q.N[a]);
+      r /= q.N[a];
+    }
+    int a0 = -1;
+#pragma unroll
+    for (int a = DIM - 1; a >= 0; --a)
+      if (g[a] % q.cells[a] == 0) a0 = a;
+    if (a0 < 0) continue;
+    long long off = 0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b)
+      if (b != a0) off = off * q.N[b] + g[b];
+    const int k = g[a0] / q.cells[a0];
+    q.u_out[e] = q.B[a0][((long long)k * q.nsteps + (q.nsteps - 1)) * q.plane_elems[a0] + off];
+  }
+}
+
+// Time levels of one axis's planes: level 0 = the initial data at the nodal
+// points, levels 1..t_nodes = the probabilistic values.
+template <int DIM>
+__global__ void pdd_levels_kernel(const WalkParams p, int axis, double plane_lo, double plane_step, int nplanes,
+                                  int t_nodes, int nb, int nc, double lob, double hb, double loc, double hc,
+                                  const double *__restrict__ u_nodes, double *__restrict__ V) {
+  const long long per = (long long)nb * nc;
+  const long long total = (long long)nplanes * (t_nodes + 1) * per;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long in_plane = e % per;
+    const int lev = (int)((e / per) % (t_nodes + 1));
+    const int k = (int)(e / (per * (t_nodes + 1)));
+    if (lev > 0) {
+      V[e] = u_nodes[((long long)k * t_nodes + (lev - 1)) * per + in_plane];
+      continue;
+    }
+    const int ib = (int)(in_plane / nc), ic = (int)(in_plane % nc);
+    double x[3] = {0.0, 0.0, 0.0};
+    int col = 0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      if (b == axis) {
+        x[b] = plane_lo + (double)k * plane_step;
+      } else {
+        x[b] = col == 0 ? lob + (double)ib * hb : loc + (double)ic * hc;
+        ++col;
+      }
+    }
+    V[e] = u0_at<DIM>(p, x);
+  }
+}
+
+}  // namespace grt
+
+using grt::DevBuf;
+
+namespace {
+
+constexpr int kPddThreads = 512;
+constexpr int kPddMaxIter = 500;
+
+int grid_for(long long total) {
+  long long b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+int check_grid(grt_ctx *c, const grt_pdd_grid *g) {
+  if (!g) return c ? c->set_error(GRT_EINVAL, "grid is NULL") : GRT_EINVAL;
+  auto bad = [&](const char *m) { return c ? c->set_error(GRT_EINVAL, m) : GRT_EINVAL; };
+  if (g->dim < 1 || g->dim > 3) return bad("grid dim must be 1, 2 or 3");
+  if (c && g->dim != c->pb.dim) return bad("grid dim differs from the problem's");
+  long long mloc = 1;
+  for (int a = 0; a < g->dim; ++a) {
+    if (!(std::isfinite(g->lo[a]) && std::isfinite(g->hi[a]) && g->hi[a] > g->lo[a]))
+      return bad("need finite lo < hi on every axis");
+    if (g->sub[a] < 1 || g->sub[a] > 4096) return bad("sub must be in [1, 4096]");
+    if (g->cells[a] < 2 || g->cells[a] > 4096) return bad("cells must be in [2, 4096]");
+    if (g->dim > 1 && (g->nodes[a] < 4 || g->nodes[a] > GRT_SPLINE_MAX_NODES))
+      return bad("nodes must be in [4, 256] on every axis");
+    mloc *= g->cells[a] - 1;
+  }
+  if (mloc > GRT_PDD_MAX_LOCAL) return bad("subdomain above GRT_PDD_MAX_LOCAL interior unknowns");
+  if (g->t_nodes < 3 || g->t_nodes + 1 > GRT_SPLINE_MAX_NODES) return bad("t_nodes must be in [3, 255]");
+  if (!(std::isfinite(g->T) && g->T > 0.0)) return bad("T must be finite and > 0");
+  if (g->nsteps < 1 || g->nsteps > 1000000) return bad("nsteps must be in [1, 1e6]");
+  return GRT_OK;
+}
+
+long long plane_nodal_points(const grt_pdd_grid *g, int a) {
+  long long m = 1;
+  for (int b = 0; b < g->dim; ++b)
+    if (b != a) m *= g->nodes[b];
+  return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grt_pdd_points(const grt_pdd_grid *g, int64_t capacity, double *x, double *t, int64_t *n_out) {
+  int rc = check_grid(nullptr, g);
+  if (rc != GRT_OK) return rc;
+  const int d = g->dim;
+  long long total = 0;
+  for (int a = 0; a < d; ++a) total += (long long)(g->sub[a] + 1) * g->t_nodes * plane_nodal_points(g, a);
+  if (n_out) *n_out = total;
+  if (capacity == 0 && !x && !t) return GRT_OK;
+  if (capacity < total || !x || !t) return GRT_EINVAL;
+  long long e = 0;
+  for (int a = 0; a < d; ++a) {
+    int others[2] = {0, 0}, no = 0;
+    for (int b = 0; b < d; ++b)
+      if (b != a) others[no++] = b;
+    const long long m = plane_nodal_points(g, a);
+    for (int k = 0; k <= g->sub[a]; ++k) {
+      const double pa = g->lo[a] + k * (g->hi[a] - g->lo[a]) / g->sub[a];
+      for (int j = 1; j <= g->t_nodes; ++j) {
+        const double tj = g->T * j / g->t_nodes;
+        for (long long i = 0; i < m; ++i) {
+          long long r = i;
+          double xi[3] = {0, 0, 0};
+          xi[a] = pa;
+          for (int o = no - 1; o >= 0; --o) {
+            const int b = others[o];
+            const long long ib = r % g->nodes[b];
+            r /= g->nodes[b];
+            xi[b] = g->lo[b] + ib * (g->hi[b] - g->lo[b]) / (g->nodes[b] - 1);
+          }
+          for (int b = 0; b < d; ++b) x[e * d + b] = xi[b];
+          t[e] = tj;
+          ++e;
+        }
+      }
+    }
+  }
+  return GRT_OK;
+}
+
+int grt_spline_grid(grt_ctx *c, int ndim, const int32_t *n_nodes, const double *lo, const double *hi,
+                    const int32_t *n_targets, const double *targets, int64_t batch, const double *d_values,
+                    double *d_out, void *stream) {
+  if (!c) return GRT_EINVAL;
+  if (ndim < 1 || ndim > 4) return c->set_error(GRT_EINVAL, "ndim must be in [1, 4]");
+  if (!n_nodes || !lo || !hi || !n_targets || !targets) return c->set_error(GRT_EINVAL, "NULL size or grid array");
+  if (batch < 0) return c->set_error(GRT_EINVAL, "batch must be >= 0");
+  long long nin = 1, nout = 1, ntot_t = 0, wsize = 0, stage = 0;
+  for (int a = 0; a < ndim; ++a) {
+    if (n_nodes[a] < 4 || n_nodes[a] > GRT_SPLINE_MAX_NODES)
+      return c->set_error(GRT_EINVAL, "n_nodes must be in [4, 256]");
+    if (n_targets[a] < 1 || n_targets[a] > (1 << 24)) return c->set_error(GRT_EINVAL, "n_targets must be >= 1");
+    if (!(std::isfinite(lo[a]) && std::isfinite(hi[a]) && hi[a] > lo[a]))
+      return c->set_error(GRT_EINVAL, "need finite lo < hi");
+    nin *= n_nodes[a];
+    nout *= n_targets[a];
+    ntot_t += n_targets[a];
+    wsize += (long long)n_targets[a] * n_nodes[a];
+  }
+  for (long long i = 0; i < ntot_t; ++i)
+    if (!std::isfinite(targets[i])) return c->set_error(GRT_EINVAL, "targets must be finite");
+  if (batch == 0) return GRT_OK;
+  if (!d_values || !d_out) return c->set_error(GRT_EINVAL, "values and out must be non-NULL");
+  // largest intermediate: axes 0..a mapped to targets, the rest still nodes
+  {
+    long long cur = nin;
+    for (int a = 0; a < ndim; ++a) {
+      cur = cur / n_nodes[a] * n_targets[a];
+      stage = cur > stage ? cur : stage;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;  // NULL: the legacy default stream, as for the solves
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  const size_t bytes_w = (size_t)(wsize + ntot_t) * sizeof(double);
+  const size_t bytes_stage = (size_t)stage * batch * sizeof(double);
+  GRT_CUDA(c, c->pdd_scratch.ensure(bytes_w + 2 * bytes_stage + 1024));
+  double *W = c->pdd_scratch.as<double>();
+  double *dtg = W + wsize;
+  double *st0 = dtg + ntot_t;
+  double *st1 = st0 + stage * batch;
+  GRT_CUDA(c, cudaMemcpyAsync(dtg, targets, ntot_t * sizeof(double), cudaMemcpyHostToDevice, s));
+  long long woff = 0, toff = 0;
+  std::vector<long long> wo(ndim), to(ndim);
+  for (int a = 0; a < ndim; ++a) {
+    wo[a] = woff;
+    to[a] = toff;
+    const double hn = (hi[a] - lo[a]) / (n_nodes[a] - 1);
+    grt::spline_weights_kernel<<<(n_nodes[a] + 63) / 64, 64, 0, s>>>(n_nodes[a], lo[a], hn, n_targets[a],
+                                                                       dtg + toff, W + woff);
+    woff += (long long)n_targets[a] * n_nodes[a];
+    toff += n_targets[a];
+  }
+  GRT_CUDA(c, cudaGetLastError());
+  // axis by axis: [batch * prod(before)] [n_a -> m_a] [prod(after)]
+  const double *src = d_values;
+  long long before = batch, after = nin;
+  for (int a = 0; a < ndim; ++a) {
+    after /= n_nodes[a];
+    double *dst = (a == ndim - 1) ? d_out : ((a % 2 == 0) ? st0 : st1);
+    const long long total = before * n_targets[a] * after;
+    grt::axis_apply_kernel<<<grid_for(total), 256, 0, s>>>(W + wo[a], n_targets[a], n_nodes[a], src, dst, before,
+                                                           after);
+    src = dst;
+    before *= n_targets[a];
+  }
+  GRT_CUDA(c, cudaGetLastError());
+  return GRT_OK;
+}
+
+int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, int32_t *info,
+                  void *stream) {
+  if (!c) return GRT_EINVAL;
+  int rc = check_grid(c, g);
+  if (rc != GRT_OK) return rc;
+  if (!d_u_nodes || !d_u_out) return c->set_error(GRT_EINVAL, "u_nodes and u_out must be non-NULL");
+  const int d = g->dim;
+  cudaStream_t s = (cudaStream_t)stream;  // NULL: the legacy default stream, as for the solves
+  GRT_CUDA(c, cudaSetDevice(c->device));
+
+  grt::PddDev q{};
+  q.dim = d;
+  long long nsub = 1;
+  q.mloc = 1;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < d;
+    q.sub[a] = on ? g->sub[a] : 1;
+    q.cells[a] = on ? g->cells[a] : 2;
+    q.N[a] = on ? g->sub[a] * g->cells[a] + 1 : 1;
+    q.m[a] = on ? g->cells[a] - 1 : 1;
+    q.lo[a] = on ? g->lo[a] : 0.0;
+    q.h[a] = on ? (g->hi[a] - g->lo[a]) / (double)(g->sub[a] * g->cells[a]) : 1.0;
+    q.inv_h2[a] = 1.0 / (q.h[a] * q.h[a]);
+    if (on) {
+      nsub *= g->sub[a];
+      q.mloc *= q.m[a];
+    }
+  }
+  q.nsteps = g->nsteps;
+  q.dt = g->T / g->nsteps;
+  q.alpha = 0.5 * q.dt * c->pb.D;
+  q.f_deg = c->pb.f_deg;
+  for (int k = 0; k <= GRT_MAX_DEG; ++k) q.f_coef[k] = k <= c->pb.f_deg ? c->pb.f_coef[k] : 0.0;
+  q.coef_pow_mask = c->pb.coef_kind != GRT_COEF_CONST ? c->pb.coef_mask : 0u;
+  q.tol2 = 1e-26;  // residual 1e-13 of the right-hand side
+  q.max_iter = kPddMaxIter;
+
+  // scratch layout: weights (time + one per axis), targets, two staging buffers,
+  // the per-axis plane arrays, the subdomain vectors, info
+  const int tn = g->t_nodes + 1;
+  long long wsz = (long long)g->nsteps * tn, tsz = g->nsteps, stage = 0, bsz = 0;
+  long long woff_ax[3] = {0, 0, 0}, toff_ax[3] = {0, 0, 0}, boff[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    woff_ax[a] = wsz;
+    toff_ax[a] = tsz;
+    wsz += (long long)q.N[a] * g->nodes[a];
+    tsz += q.N[a];
+  }
+  for (int a = 0; a < d; ++a) {
+    const long long np = g->sub[a] + 1;
+    long long pn = 1, pf = 1;
+    for (int b = 0; b < d; ++b)
+      if (b != a) {
+        pn *= g->nodes[b];
+        pf *= q.N[b];
+      }
+    q.plane_elems[a] = pf;
+    // stages: levels [np][tn][pn] -> [np][nsteps][pn] -> [np][nsteps][N_b][n_c]
+    long long s0 = np * tn * pn, s1 = np * g->nsteps * pn, s2 = s1;
+    if (d == 3) {
+      int bs[2], nb = 0;
+      for (int b = 0; b < d; ++b)
+        if (b != a) bs[nb++] = b;
+      s2 = np * g->nsteps * (long long)q.N[bs[0]] * g->nodes[bs[1]];
+    }
+    const long long mx = s0 > s1 ? (s0 > s2 ? s0 : s2) : (s1 > s2 ? s1 : s2);
+    stage = mx > stage ? mx : stage;
+    boff[a] = bsz;
+    bsz += np * g->nsteps * pf;
+  }
+  const long long vsz = nsub * 6 * (long long)q.mloc;
+  const size_t total = (size_t)(wsz + tsz + 2 * stage + bsz + vsz) * sizeof(double) + 256;
+  GRT_CUDA(c, c->pdd_scratch.ensure(total));
+  double *base = c->pdd_scratch.as<double>();
+  double *W = base, *tg = W + wsz, *st0 = tg + tsz, *st1 = st0 + stage, *Bb = st1 + stage, *V = Bb + bsz;
+  int *dinfo = reinterpret_cast<int *>(V + vsz);
+  q.work = V;
+  q.info = dinfo;
+  q.u_out = d_u_out;
+  for (int a = 0; a < 3; ++a) q.B[a] = a < d ? Bb + boff[a] : nullptr;
+
+  // target coordinates (host-built, one small copy): t_1..t_N, then each axis's FD nodes
+  std::vector<double> ht((size_t)tsz);
+  for (int n = 0; n < g->nsteps; ++n) ht[n] = q.dt * (n + 1);
+  for (int a = 0; a < d; ++a)
+    for (int i = 0; i < q.N[a]; ++i) ht[(size_t)toff_ax[a] + i] = q.lo[a] + i * q.h[a];
+  GRT_CUDA(c, cudaMemcpyAsync(tg, ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  GRT_CUDA(c, cudaMemsetAsync(dinfo, 0, 2 * sizeof(int), s));
+  // weights: time axis (t_nodes + 1 uniform levels over [0, T]) and every space axis
+  grt::spline_weights_kernel<<<1, 256, 0, s>>>(tn, 0.0, g->T / g->t_nodes, g->nsteps, tg, W);
+  for (int a = 0; a < d; ++a)
+    grt::spline_weights_kernel<<<(g->nodes[a] + 63) / 64, 64, 0, s>>>(
+        g->nodes[a], q.lo[a], (g->hi[a] - g->lo[a]) / (g->nodes[a] - 1), q.N[a], tg + toff_ax[a], W + woff_ax[a]);
+  GRT_CUDA(c, cudaGetLastError());
+
+  // spline every axis's planes
+  long long in_off = 0;
+  for (int a = 0; a < d; ++a) {
+    const int np = g->sub[a] + 1;
+    int bs[2] = {-1, -1}, nb = 0;
+    for (int b = 0; b < d; ++b)
+      if (b != a) bs[nb++] = b;
+    const int nbn = nb > 0 ? g->nodes[bs[0]] : 1, ncn = nb > 1 ? g->nodes[bs[1]] : 1;
+    const double lob = nb > 0 ? q.lo[bs[0]] : 0.0, hb = nb > 0 ? (g->hi[bs[0]] - g->lo[bs[0]]) / (nbn - 1) : 0.0;
+    const double loc = nb > 1 ? q.lo[bs[1]] : 0.0, hc = nb > 1 ? (g->hi[bs[1]] - g->lo[bs[1]]) / (ncn - 1) : 0.0;
+    const long long pn = (long long)nbn * ncn;
+    const long long lev_total = (long long)np * tn * pn;
+    const double pstep = (g->hi[a] - g->lo[a]) / g->sub[a];
+    switch (d) {
+    case 1:
+      grt::pdd_levels_kernel<1><<<grid_for(lev_total), 256, 0, s>>>(c->base, a, q.lo[a], pstep, np, g->t_nodes,
+                                                                      nbn, ncn, lob, hb, loc, hc, d_u_nodes + in_off,
+                                                                      st0);
+      break;
+    case 2:
+      grt::pdd_levels_kernel<2><<<grid_for(lev_total), 256, 0, s>>>(c->base, a, q.lo[a], pstep, np, g->t_nodes,
+                                                                      nbn, ncn, lob, hb, loc, hc, d_u_nodes + in_off,
+                                                                      st0);
+      break;
+    default:
+      grt::pdd_levels_kernel<3><<<grid_for(lev_total), 256, 0, s>>>(c->base, a, q.lo[a], pstep, np, g->t_nodes,
+                                                                      nbn, ncn, lob, hb, loc, hc, d_u_nodes + in_off,
+                                                                      st0);
+      break;
+    }
+    in_off += (long long)np * g->t_nodes * pn;
+    double *Ba = Bb + boff[a];
+    // time: [np][tn][pn] -> [np][nsteps][pn]
+    double *dst = nb == 0 ? Ba : st1;
+    grt::axis_apply_kernel<<<grid_for((long long)np * g->nsteps * pn), 256, 0, s>>>(W, g->nsteps, tn, st0, dst, np,
+                                                                                    pn);
+    if (nb >= 1) {
+      // first in-plane axis: [np*nsteps][nbn][ncn] -> [np*nsteps][N_b][ncn]
+      double *dst2 = nb == 1 ? Ba : st0;
+      const long long outer = (long long)np * g->nsteps;
+      grt::axis_apply_kernel<<<grid_for(outer * q.N[bs[0]] * ncn), 256, 0, s>>>(W + woff_ax[bs[0]], q.N[bs[0]], nbn,
+                                                                                 st1, dst2, outer, ncn);
+      if (nb == 2) {
+        const long long outer2 = outer * q.N[bs[0]];
+        grt::axis_apply_kernel<<<grid_for(outer2 * q.N[bs[1]]), 256, 0, s>>>(W + woff_ax[bs[1]], q.N[bs[1]], ncn,
+                                                                             st0, Ba, outer2, 1);
+      }
+    }
+  }
+  GRT_CUDA(c, cudaGetLastError());
+
+  // subdomain solves and the plane nodes of the output
+  long long ntot = 1;
+  for (int a = 0; a < d; ++a) ntot *= q.N[a];
+  switch (d) {
+  case 1:
+    grt::cn_subdomain_kernel<1, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    grt::pdd_planes_kernel<1><<<grid_for(ntot), 256, 0, s>>>(q);
+    break;
+  case 2:
+    grt::cn_subdomain_kernel<2, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    grt::pdd_planes_kernel<2><<<grid_for(ntot), 256, 0, s>>>(q);
+    break;
+  default:
+    grt::cn_subdomain_kernel<3, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    grt::pdd_planes_kernel<3><<<grid_for(ntot), 256, 0, s>>>(q);
+    break;
+  }
+  GRT_CUDA(c, cudaGetLastError());
+  if (info) {
+    int h[2] = {0, 0};
+    GRT_CUDA(c, cudaMemcpyAsync(h, dinfo, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GRT_CUDA(c, cudaStreamSynchronize(s));
+    info[0] = h[0];
+    info[1] = h[1];
+  }
+  return GRT_OK;
+}
+
+}  // extern "C"

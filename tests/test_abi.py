@@ -3,6 +3,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import workloads
@@ -80,3 +81,21 @@ def test_null_arguments(lib):
     lib.grt_plan_destroy(None)
     assert lib.grt_solve(None, 0, None, None, None, 0, 0, 0, 0, 0, None, None, None, None) == -1
     assert lib.grt_plan_launches(None) == 0
+
+
+def test_pdd_points_match_the_oracle_layout(lib):
+    # grt_pdd_points is host-only: the nodal points and their order are the oracle's
+    import paper_2402_06491_gb300 as pkg
+    from oracle import pdd
+
+    for g in (dict(dim=1, lo=[-1.0], hi=[2.0], sub=[3], cells=[4], nodes=[4], t_nodes=3, T=0.7, nsteps=5),
+              dict(dim=2, lo=[0.0, -1.0], hi=[3.0, 1.0], sub=[3, 2], cells=[4, 6], nodes=[7, 5], t_nodes=4, T=1.0,
+                   nsteps=8),
+              dict(dim=3, lo=[0.0] * 3, hi=[4.0] * 3, sub=[4] * 3, cells=[8] * 3, nodes=[17] * 3, t_nodes=4, T=1.0,
+                   nsteps=40)):
+        x, t = pkg.grt_pdd_points(g)
+        xo, to = pdd.points(g)
+        assert x.shape == xo.shape and np.allclose(x, xo, rtol=0, atol=1e-14) and np.array_equal(t, to)
+    with pytest.raises(pkg.GrtError):
+        pkg.grt_pdd_points(dict(dim=2, lo=[0.0, 0.0], hi=[1.0, 1.0], sub=[2, 2], cells=[4, 4], nodes=[3, 5], t_nodes=4,
+                                T=1.0, nsteps=4))
