@@ -314,21 +314,21 @@ int grt_spline_grid(grt_ctx *ctx, int ndim, const int32_t *n_nodes, const double
                     double *d_out, void *stream);
 
 /* PDD geometry.  The box prod_a [lo[a], hi[a]] is cut into sub[a] equal
- * subdomains along axis a; each has cells[a] >= 2 finite-difference cells per
- * axis, so the global grid has N[a] = sub[a] cells[a] + 1 nodes.  The planes
- * are the grid planes bounding a subdomain, outer faces included (the outer
- * faces carry probabilistic artificial Dirichlet data, the use the text after
- * Example 4 describes).  On every plane of axis a the nodal points are the
- * tensor grid of nodes[b] >= 4 uniform points over [lo[b], hi[b]] (both ends
- * included) along each other axis b, at the t_nodes >= 3 time levels
- * t_j = T j / t_nodes, j = 1..t_nodes (t = 0 is the initial data itself).
- * Crank-Nicolson takes nsteps >= 1 steps of T / nsteps. */
+ * subdomains along axis a; each has cells[a] in [2, 65] finite-difference
+ * cells per axis, so the global grid has N[a] = sub[a] cells[a] + 1 nodes.
+ * The planes are the grid planes bounding a subdomain, outer faces included
+ * (the outer faces carry probabilistic artificial Dirichlet data, the use the
+ * text after Example 4 describes).  On every plane of axis a the nodal points
+ * are the tensor grid of nodes[b] >= 4 uniform points over [lo[b], hi[b]]
+ * (both ends included) along each other axis b, at the t_nodes >= 3 time
+ * levels t_j = T j / t_nodes, j = 1..t_nodes (t = 0 is the initial data
+ * itself).  Crank-Nicolson takes nsteps >= 1 steps of T / nsteps. */
 typedef struct grt_pdd_grid {
     int32_t dim;        /* 1..3, the context's dimension */
     double lo[3], hi[3];
     int32_t sub[3];
     int32_t cells[3];
-    int32_t nodes[3];   /* entry a unused (the plane's own axis) */
+    int32_t nodes[3];   /* entry a unused by the planes of axis a */
     int32_t t_nodes;
     double T;
     int32_t nsteps;
@@ -341,9 +341,9 @@ typedef struct grt_pdd_grid {
  * the order grt_pdd_solve reads their values: planes axis-major (axis 0 planes
  * k = 0..sub[0], then axis 1, ...), then time level j = 1..t_nodes, then the
  * in-plane nodes row-major over the other axes in ascending order.  x [n][dim]
- * and t [n] are HOST arrays of `capacity` points (may be NULL with capacity 0
- * to query); *n_out receives the count.  GRT_EINVAL for a bad grid or a
- * capacity below the count. */
+ * and t [n] are HOST arrays of `capacity` points (x and t NULL with capacity
+ * 0 to query the count); *n_out receives the count.  GRT_EINVAL for a bad
+ * grid or a capacity below the count. */
 int grt_pdd_points(const grt_pdd_grid *g, int64_t capacity, double *x, double *t, int64_t *n_out);
 
 /* The PDD solution at t = T on the global grid.  d_u_nodes: DEVICE values at
@@ -353,22 +353,19 @@ int grt_pdd_points(const grt_pdd_grid *g, int64_t capacity, double *x, double *t
  *      coordinates to the finite-difference nodes at t_n = n T / nsteps,
  *      n = 1..nsteps, with the initial data as the t = 0 level;
  *   2. one thread block per subdomain runs all nsteps steps of the linearly
- *      implicit Crank-Nicolson scheme
+ *      implicit Crank-Nicolson scheme (Sec. 3, "Local solver")
  *        (I - dt/2 D Lap_h) u^{n+1} = (I + dt/2 D Lap_h) u^n + dt f(u*, x, t_{n+1/2}),
  *        u* = (3 u^n - u^{n-1}) / 2  (u^0 on the first step),
  *      Dirichlet data from step 1 (the initial data at t_0), f the context's
- *      f with its variable coefficients, each linear system solved by
- *      conjugate gradients to a residual of 1e-13 of its right-hand side;
+ *      f with its variable coefficients; each step's linear system is solved
+ *      exactly by fast diagonalisation (sine transforms along each axis);
  *   3. plane nodes of d_u_out take the spline at T (an edge node takes the
  *      plane of its lowest axis), subdomain interiors the solves.
- * info (HOST, optional, int32[2]): [0] the largest CG iteration count of any
- * step, [1] the number of steps that stopped at the iteration cap (500)
- * without reaching the tolerance; when info is given the call waits for the
- * stream.  Work memory is held by the context: calls on one context must not
- * overlap in time.  Enqueued on `stream` (NULL = legacy default stream).
- * GRT_EINVAL for a bad grid or a subdomain above GRT_PDD_MAX_LOCAL unknowns. */
-int grt_pdd_solve(grt_ctx *ctx, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, int32_t *info,
-                  void *stream);
+ * Work memory is held by the context: calls on one context must not overlap
+ * in time.  Enqueued on `stream` (NULL = legacy default stream); returns after
+ * enqueueing.  GRT_EINVAL for a bad grid, a dimension other than the
+ * context's, or a subdomain above GRT_PDD_MAX_LOCAL unknowns. */
+int grt_pdd_solve(grt_ctx *ctx, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, void *stream);
 
 #ifdef __cplusplus
 }

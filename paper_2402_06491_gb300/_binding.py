@@ -110,7 +110,7 @@ def _load():
         "grt_server_stats": ([_vp, u64p, u64p, u64p, u64p, u64p, u64p], i32),
         "grt_spline_grid": ([_vp, i32, i32p, f64p, f64p, i32p, f64p, i64, _vp, _vp, _vp], i32),
         "grt_pdd_points": ([_P(grt_pdd_grid), i64, f64p, f64p, _P(ctypes.c_int64)], i32),
-        "grt_pdd_solve": ([_vp, _P(grt_pdd_grid), _vp, _vp, i32p, _vp], i32),
+        "grt_pdd_solve": ([_vp, _P(grt_pdd_grid), _vp, _vp, _vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -541,19 +541,15 @@ def grt_pdd_points(grid: dict):
     return x, t
 
 
-def grt_pdd_solve(ctx: Context, grid: dict, u_nodes, u_out, stream=None, info: bool = True):
-    """PDD solution at T on the global grid into the device buffer u_out (N[0] x ... row-major).
-    u_nodes: device values at grt_pdd_points.  Returns [max CG iterations, capped steps] when info."""
+def grt_pdd_solve(ctx: Context, grid: dict, u_nodes, u_out, stream=None) -> None:
+    """Enqueue the PDD solution at T on the global grid into the device buffer u_out (N[0] x ... row-major).
+    u_nodes: device values at grt_pdd_points."""
     lib = _load()
     gs = pdd_grid_struct(grid)
     sh = None
     if stream is not None:
         sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    inf = np.zeros(2, np.int32)
-    rc = lib.grt_pdd_solve(ctx.handle, ctypes.byref(gs), _devptr(u_nodes), _devptr(u_out),
-                           _ptr(inf, ctypes.c_int32) if info else None, sh)
-    _check(rc, ctx.handle)
-    return [int(v) for v in inf] if info else None
+    _check(lib.grt_pdd_solve(ctx.handle, ctypes.byref(gs), _devptr(u_nodes), _devptr(u_out), sh), ctx.handle)
 
 
 def grt_spline_grid(ctx: Context, n_nodes, lo, hi, targets, values, out, batch: int = 1, stream=None) -> None:

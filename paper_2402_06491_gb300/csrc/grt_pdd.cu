@@ -7,9 +7,10 @@
 //     system of a unit data vector by elimination, then the cubic at every
 //     target) and an axis-contraction kernel applied once per axis, FP64;
 //   * local solver: one thread block per subdomain runs every time step with
-//     its vectors in global memory (L2-resident: a few MB in all) and a
-//     conjugate-gradient solve per step; the subdomains share nothing, which
-//     is the decoupling the method is built on (Sec. 3, "Local solver").
+//     its four vectors in shared memory (global memory beyond 200 KB) and an
+//     exact fast-diagonalisation solve per step (DST-I along each axis as small
+//     dense FP64 contractions); the subdomains share nothing, which is the
+//     decoupling the method is built on (Sec. 3, "Local solver").
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -107,13 +108,29 @@ struct PddDev {
   int f_deg;
   double f_coef[GRT_MAX_DEG + 1];
   uint32_t coef_pow_mask;    // powers k whose coefficient is b_k gamma(x, t)
-  double *work;              // [nsub][6][mloc]
+  const double *S[3];        // per axis: the m x m orthonormal DST-I matrix
+  const double *mu[3];       // per axis: eigenvalues of the 1-D Dirichlet second difference
+  double *work;              // [nsub][4][mloc] when the vectors do not fit in shared memory
   int mloc;
-  double tol2;
-  int max_iter;
-  int *info;                 // [0] largest CG iteration count, [1] steps at the cap
+  int use_smem;
   double *u_out;
 };
+
+// S[i][j] = sqrt(2/(m+1)) sin(pi (i+1)(j+1)/(m+1)) (symmetric, orthonormal, its own
+// inverse) and mu[k] = -(4/h^2) sin^2(pi (k+1) / (2 (m+1))): the eigenvectors and
+// eigenvalues of the second difference with zero Dirichlet ends.  The product
+// (i+1)(j+1) is reduced modulo 2(m+1) in integers before the sine.
+__global__ void dst_tables_kernel(int m, double h, double *__restrict__ S, double *__restrict__ mu) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int i = e / m, j = e % m;
+  const int r = ((i + 1) * (j + 1)) % (2 * (m + 1));
+  S[e] = sqrt(2.0 / (double)(m + 1)) * sinpi((double)r / (double)(m + 1));
+  if (j == 0) {
+    const double sv = sinpi((double)(i + 1) / (2.0 * (double)(m + 1)));
+    mu[i] = -4.0 / (h * h) * sv * sv;
+  }
+}
 
 // initial data at a point (FP64, the walk's own formulas with zero displacement)
 template <int DIM> __device__ __forceinline__ double u0_at(const WalkParams &p, const double (&x)[3]) {
@@ -163,19 +180,6 @@ __device__ __forceinline__ double ring_value(const WalkParams &p, const PddDev &
   return q.B[a][((long long)k * q.nsteps + (n - 1)) * q.plane_elems[a] + off];
 }
 
-template <int NT> __device__ __forceinline__ double block_sum(double v, double *red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();  // red[] free from the previous use
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < NT / 32; ++i) s += red[i];  // fixed order: deterministic
-  return s;
-}
-
 template <int DIM> __device__ __forceinline__ void local_index(const PddDev &q, int l, int (&i)[3]) {
   i[0] = i[1] = i[2] = 0;
 #pragma unroll
@@ -185,25 +189,32 @@ template <int DIM> __device__ __forceinline__ void local_index(const PddDev &q, 
   }
 }
 
-// (A v)_l = v_l - alpha Lap_h^0 v at local node l (zero ring)
-template <int DIM>
-__device__ __forceinline__ double apply_A(const PddDev &q, const double *__restrict__ v, int l, const int (&i)[3],
-                                          const int (&stride)[3]) {
-  const double c = v[l];
-  double lap = 0.0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const double left = i[a] > 0 ? v[l - stride[a]] : 0.0;
-    const double right = i[a] < q.m[a] - 1 ? v[l + stride[a]] : 0.0;
-    lap += (left + right - 2.0 * c) * q.inv_h2[a];
+// dst = S_ax applied along axis ax of src (one output per thread-iteration)
+template <int DIM, int NT>
+__device__ __forceinline__ void dst_axis(const PddDev &q, int ax, const int (&stride)[3], const double *src,
+                                         double *dst) {
+  const int m = q.m[ax], st = stride[ax];
+  const double *__restrict__ S = q.S[ax];
+  for (int l = threadIdx.x; l < q.mloc; l += NT) {
+    int i[3];
+    local_index<DIM>(q, l, i);
+    const double *col = src + (l - i[ax] * st);
+    const double *row = S + i[ax] * m;
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) acc = fma(__ldg(row + j), col[j * st], acc);
+    dst[l] = acc;
   }
-  return c - q.alpha * lap;
 }
 
-// One block per subdomain: every Crank-Nicolson step, CG per step.
+// One block per subdomain runs every Crank-Nicolson step.  Each step's system
+// (I - alpha Lap_h) x = b is solved exactly by fast diagonalisation (Lynch,
+// Rice and Thomas, Numer. Math. 6, 1964): the Dirichlet Laplacian of a box is
+// diagonal in the tensor product of 1-D sine bases, so x = S (S b / (1 - alpha
+// sum_a mu_a)) with S the DST-I along every axis -- 2 d small dense
+// contractions per step, no iteration and no block-wide reduction.
 template <int DIM, int NT>
 __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, const PddDev q) {
-  __shared__ double red[NT / 32];
+  extern __shared__ double smem_vec[];
   const int sid = blockIdx.x;
   int s[3] = {0, 0, 0};
   {
@@ -215,8 +226,8 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
     }
   }
   const int mloc = q.mloc;
-  double *u = q.work + (size_t)sid * 6 * mloc;
-  double *up = u + mloc, *x = up + mloc, *r = x + mloc, *pv = r + mloc, *Ap = pv + mloc;
+  double *base = q.use_smem ? smem_vec : q.work + (size_t)sid * 4 * mloc;
+  double *u = base, *up = u + mloc, *va = up + mloc, *vb = va + mloc;
   int stride[3] = {1, 1, 1};
 #pragma unroll
   for (int a = DIM - 2; a >= 0; --a) stride[a] = stride[a + 1] * q.m[a + 1];
@@ -241,14 +252,9 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
   }
   __syncthreads();
 
-  int it_max = 0, fails = 0;
   for (int n = 0; n < q.nsteps; ++n) {
-    // initial guess: the linear extrapolation 2 u^n - u^{n-1} (u^0 on the first step)
-    for (int l = threadIdx.x; l < mloc; l += NT) x[l] = n == 0 ? u[l] : 2.0 * u[l] - up[l];
-    __syncthreads();
-    // right-hand side and the first residual r = b - A x
+    // right-hand side b = u + alpha Lap_h u (ring at t_n) + alpha (ring part at t_{n+1}) + dt f(u*)
     const double th = ((double)n + 0.5) * q.dt;
-    double bb = 0.0, rr0 = 0.0;
     for (int l = threadIdx.x; l < mloc; l += NT) {
       int i[3], gi[3];
       double xc[3];
@@ -266,50 +272,41 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
         ring1 += rn * q.inv_h2[a];
       }
       const double ustar = n == 0 ? c : 1.5 * c - 0.5 * up[l];
-      const double b = c + q.alpha * lap + q.alpha * ring1 + q.dt * f_at<DIM>(p, q, xc, th, ustar);
-      const double res = b - apply_A<DIM>(q, x, l, i, stride);
-      r[l] = res;
-      pv[l] = res;
-      bb += b * b;
-      rr0 += res * res;
+      va[l] = c + q.alpha * lap + q.alpha * ring1 + q.dt * f_at<DIM>(p, q, xc, th, ustar);
     }
-    bb = block_sum<NT>(bb, red);
-    double rr = block_sum<NT>(rr0, red);
-    const double stop = q.tol2 * bb;
-    int it = 0;
-    while (rr > stop && it < q.max_iter) {
-      double pap = 0.0;
-      for (int l = threadIdx.x; l < mloc; l += NT) {
-        int i[3];
-        local_index<DIM>(q, l, i);
-        const double a = apply_A<DIM>(q, pv, l, i, stride);
-        Ap[l] = a;
-        pap += pv[l] * a;
-      }
-      pap = block_sum<NT>(pap, red);
-      const double step = rr / pap;
-      double rn = 0.0;
-      for (int l = threadIdx.x; l < mloc; l += NT) {
-        x[l] = fma(step, pv[l], x[l]);
-        const double v = fma(-step, Ap[l], r[l]);
-        r[l] = v;
-        rn += v * v;
-      }
-      rn = block_sum<NT>(rn, red);
-      const double beta = rn / rr;
-      for (int l = threadIdx.x; l < mloc; l += NT) pv[l] = fma(beta, pv[l], r[l]);
-      __syncthreads();
-      rr = rn;
-      ++it;
-    }
-    it_max = it > it_max ? it : it_max;
-    if (rr > stop) ++fails;
-    // rotate: u^{n-1} <- u^n, u^n <- x
-    double *t0 = up;
-    up = u;
-    u = x;
-    x = t0;
     __syncthreads();
+    double *src = va, *dst = vb;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {  // into the sine basis
+      dst_axis<DIM, NT>(q, a, stride, src, dst);
+      __syncthreads();
+      double *t = src;
+      src = dst;
+      dst = t;
+    }
+    for (int l = threadIdx.x; l < mloc; l += NT) {  // divide by the eigenvalues of I - alpha Lap_h
+      int i[3];
+      local_index<DIM>(q, l, i);
+      double lam = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) lam += q.mu[a][i[a]];
+      src[l] = src[l] / (1.0 - q.alpha * lam);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {  // back (S is its own inverse)
+      dst_axis<DIM, NT>(q, a, stride, src, dst);
+      __syncthreads();
+      double *t = src;
+      src = dst;
+      dst = t;
+    }
+    // rotate: u^{n-1} <- u^n, u^n <- the solution; the two freed vectors are the next scratch
+    double *old_up = up;
+    up = u;
+    u = src;
+    va = old_up;
+    vb = dst;
   }
   for (int l = threadIdx.x; l < mloc; l += NT) {
     int i[3], gi[3];
@@ -319,10 +316,6 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
 #pragma unroll
     for (int a = 0; a < DIM; ++a) off = off * q.N[a] + gi[a];
     q.u_out[off] = u[l];
-  }
-  if (threadIdx.x == 0) {
-    atomicMax(q.info, it_max);
-    if (fails) atomicAdd(q.info + 1, fails);
   }
 }
 
@@ -394,7 +387,8 @@ using grt::DevBuf;
 namespace {
 
 constexpr int kPddThreads = 512;
-constexpr int kPddMaxIter = 500;
+constexpr int kPddMaxAxis = 64;                   // interior nodes per axis of a subdomain (dense DST)
+constexpr size_t kPddSmemBytes = 200u * 1024u;    // the four vectors in shared memory up to this size
 
 int grid_for(long long total) {
   long long b = (total + 255) / 256;
@@ -412,7 +406,7 @@ int check_grid(grt_ctx *c, const grt_pdd_grid *g) {
     if (!(std::isfinite(g->lo[a]) && std::isfinite(g->hi[a]) && g->hi[a] > g->lo[a]))
       return bad("need finite lo < hi on every axis");
     if (g->sub[a] < 1 || g->sub[a] > 4096) return bad("sub must be in [1, 4096]");
-    if (g->cells[a] < 2 || g->cells[a] > 4096) return bad("cells must be in [2, 4096]");
+    if (g->cells[a] < 2 || g->cells[a] > kPddMaxAxis + 1) return bad("cells must be in [2, 65]");
     if (g->dim > 1 && (g->nodes[a] < 4 || g->nodes[a] > GRT_SPLINE_MAX_NODES))
       return bad("nodes must be in [4, 256] on every axis");
     mloc *= g->cells[a] - 1;
@@ -543,8 +537,7 @@ int grt_spline_grid(grt_ctx *c, int ndim, const int32_t *n_nodes, const double *
   return GRT_OK;
 }
 
-int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, int32_t *info,
-                  void *stream) {
+int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, void *stream) {
   if (!c) return GRT_EINVAL;
   int rc = check_grid(c, g);
   if (rc != GRT_OK) return rc;
@@ -577,11 +570,9 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   q.f_deg = c->pb.f_deg;
   for (int k = 0; k <= GRT_MAX_DEG; ++k) q.f_coef[k] = k <= c->pb.f_deg ? c->pb.f_coef[k] : 0.0;
   q.coef_pow_mask = c->pb.coef_kind != GRT_COEF_CONST ? c->pb.coef_mask : 0u;
-  q.tol2 = 1e-26;  // residual 1e-13 of the right-hand side
-  q.max_iter = kPddMaxIter;
 
   // scratch layout: weights (time + one per axis), targets, two staging buffers,
-  // the per-axis plane arrays, the subdomain vectors, info
+  // the per-axis plane arrays, the DST tables, the subdomain vectors (when not in shared memory)
   const int tn = g->t_nodes + 1;
   long long wsz = (long long)g->nsteps * tn, tsz = g->nsteps, stage = 0, bsz = 0;
   long long woff_ax[3] = {0, 0, 0}, toff_ax[3] = {0, 0, 0}, boff[3] = {0, 0, 0};
@@ -613,14 +604,24 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
     boff[a] = bsz;
     bsz += np * g->nsteps * pf;
   }
-  const long long vsz = nsub * 6 * (long long)q.mloc;
-  const size_t total = (size_t)(wsz + tsz + 2 * stage + bsz + vsz) * sizeof(double) + 256;
+  long long dsz = 0, doff[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    doff[a] = dsz;
+    dsz += (long long)q.m[a] * q.m[a] + q.m[a];
+  }
+  const size_t vec_bytes = 4 * (size_t)q.mloc * sizeof(double);
+  q.use_smem = vec_bytes <= kPddSmemBytes ? 1 : 0;
+  const long long vsz = q.use_smem ? 0 : nsub * 4 * (long long)q.mloc;
+  const size_t total = (size_t)(wsz + tsz + 2 * stage + bsz + dsz + vsz) * sizeof(double) + 256;
   GRT_CUDA(c, c->pdd_scratch.ensure(total));
   double *base = c->pdd_scratch.as<double>();
-  double *W = base, *tg = W + wsz, *st0 = tg + tsz, *st1 = st0 + stage, *Bb = st1 + stage, *V = Bb + bsz;
-  int *dinfo = reinterpret_cast<int *>(V + vsz);
+  double *W = base, *tg = W + wsz, *st0 = tg + tsz, *st1 = st0 + stage, *Bb = st1 + stage, *Dt = Bb + bsz;
+  double *V = Dt + dsz;
   q.work = V;
-  q.info = dinfo;
+  for (int a = 0; a < 3; ++a) {
+    q.S[a] = a < d ? Dt + doff[a] : nullptr;
+    q.mu[a] = a < d ? Dt + doff[a] + (long long)q.m[a] * q.m[a] : nullptr;
+  }
   q.u_out = d_u_out;
   for (int a = 0; a < 3; ++a) q.B[a] = a < d ? Bb + boff[a] : nullptr;
 
@@ -630,7 +631,9 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   for (int a = 0; a < d; ++a)
     for (int i = 0; i < q.N[a]; ++i) ht[(size_t)toff_ax[a] + i] = q.lo[a] + i * q.h[a];
   GRT_CUDA(c, cudaMemcpyAsync(tg, ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  GRT_CUDA(c, cudaMemsetAsync(dinfo, 0, 2 * sizeof(int), s));
+  for (int a = 0; a < d; ++a)
+    grt::dst_tables_kernel<<<(q.m[a] * q.m[a] + 127) / 128, 128, 0, s>>>(q.m[a], q.h[a], Dt + doff[a],
+                                                                          Dt + doff[a] + (long long)q.m[a] * q.m[a]);
   // weights: time axis (t_nodes + 1 uniform levels over [0, T]) and every space axis
   grt::spline_weights_kernel<<<1, 256, 0, s>>>(tn, 0.0, g->T / g->t_nodes, g->nsteps, tg, W);
   for (int a = 0; a < d; ++a)
@@ -692,28 +695,28 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   // subdomain solves and the plane nodes of the output
   long long ntot = 1;
   for (int a = 0; a < d; ++a) ntot *= q.N[a];
+  const size_t smem = q.use_smem ? vec_bytes : 0;
   switch (d) {
   case 1:
-    grt::cn_subdomain_kernel<1, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<1, kPddThreads>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
+    grt::cn_subdomain_kernel<1, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
     grt::pdd_planes_kernel<1><<<grid_for(ntot), 256, 0, s>>>(q);
     break;
   case 2:
-    grt::cn_subdomain_kernel<2, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<2, kPddThreads>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
+    grt::cn_subdomain_kernel<2, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
     grt::pdd_planes_kernel<2><<<grid_for(ntot), 256, 0, s>>>(q);
     break;
   default:
-    grt::cn_subdomain_kernel<3, kPddThreads><<<(unsigned)nsub, kPddThreads, 0, s>>>(c->base, q);
+    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<3, kPddThreads>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
+    grt::cn_subdomain_kernel<3, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
     grt::pdd_planes_kernel<3><<<grid_for(ntot), 256, 0, s>>>(q);
     break;
   }
   GRT_CUDA(c, cudaGetLastError());
-  if (info) {
-    int h[2] = {0, 0};
-    GRT_CUDA(c, cudaMemcpyAsync(h, dinfo, sizeof(h), cudaMemcpyDeviceToHost, s));
-    GRT_CUDA(c, cudaStreamSynchronize(s));
-    info[0] = h[0];
-    info[1] = h[1];
-  }
   return GRT_OK;
 }
 

@@ -3,8 +3,8 @@
   * grt_spline_grid against the oracle's tensor-product not-a-knot spline
     (1e-12 of the data's size: both are FP64 evaluations of one linear map);
   * grt_pdd_solve against the oracle's PDD on the same nodal values: the spline
-    stages agree to rounding and each Crank-Nicolson step is solved by CG to a
-    residual of 1e-13 of its right-hand side (the oracle solves exactly), so the
+    stages agree to rounding and both sides solve each Crank-Nicolson system
+    exactly (sine transforms: dense on the GPU, FFT-based in the oracle), so the
     solutions agree to 1e-10 of max |u| after tens of steps;
   * end to end on the 3-D interface problem: point solves on the GPU at the
     PDD nodal points, the PDD on the GPU, and the oracle's global
@@ -64,7 +64,8 @@ def _pdd_problem(dim):
 
 
 @pytest.mark.parametrize("dim,sub,cells,nodes", [(1, [4], [9], [4]), (2, [3, 2], [7, 5], [7, 6]),
-                                                 (3, [2, 3, 2], [6, 5, 7], [6, 7, 5])])
+                                                 (3, [2, 3, 2], [6, 5, 7], [6, 7, 5]),
+                                                 (3, [1, 1, 2], [20, 20, 20], [5, 5, 5])])  # vectors in global memory
 def test_pdd_solve_parity(grt, torch, dim, sub, cells, nodes):
     g = dict(dim=dim, lo=[0.0] * dim, hi=[float(s) for s in sub], sub=sub, cells=cells, nodes=nodes, t_nodes=4,
              T=0.6, nsteps=24)
@@ -74,11 +75,10 @@ def test_pdd_solve_parity(grt, torch, dim, sub, cells, nodes):
     ctx = grt.grt_create(pb, 0)
     N = [sub[a] * cells[a] + 1 for a in range(dim)]
     out = torch.empty(N, dtype=torch.float64, device="cuda")
-    info = grt.grt_pdd_solve(ctx, g, torch.from_numpy(u_nodes).cuda(), out)
+    grt.grt_pdd_solve(ctx, g, torch.from_numpy(u_nodes).cuda(), out)
     G = out.cpu().numpy()
     ctx.close()
     O = pdd.pdd_solve(pb, g, u_nodes)
-    assert info[0] > 0 and info[1] == 0, info
     assert np.allclose(G, O, rtol=0, atol=1e-10 * np.abs(O).max()), np.abs(G - O).max()
 
 
@@ -88,7 +88,7 @@ def test_pdd_rejects_bad_grids(grt):
                 nsteps=8)
     for bad in (dict(good, cells=[1, 4]), dict(good, nodes=[3, 5]), dict(good, t_nodes=2), dict(good, dim=3,
                 lo=[0.0] * 3, hi=[1.0] * 3, sub=[1] * 3, cells=[4] * 3, nodes=[4] * 3),
-                dict(good, cells=[300, 300])):
+                dict(good, cells=[66, 4])):
         with pytest.raises(grt.GrtError):
             grt.grt_pdd_solve(ctx, bad, 0, 0)
     ctx.close()
@@ -133,12 +133,12 @@ def test_pdd_3d_end_to_end_against_the_global_solve(grt, torch):
     u = torch.empty(n, dtype=torch.float64, device="cuda")
     grt.grt_plan_execute(plan, dx, dtt, 0, 0, u)
     out = torch.empty((33, 33, 33), dtype=torch.float64, device="cuda")
-    info = grt.grt_pdd_solve(ctx, g, u, out)
+    grt.grt_pdd_solve(ctx, g, u, out)
     G = out.cpu().numpy()
     u_nodes = u.cpu().numpy()
     plan.close()
     ctx.close()
-    assert info[1] == 0 and np.isfinite(u_nodes).all()
+    assert np.isfinite(u_nodes).all() and np.isfinite(G).all()
     # parity of the PDD stages on these nodal values
     O = pdd.pdd_solve(pb, g, u_nodes)
     assert np.allclose(G, O, rtol=0, atol=1e-10 * np.abs(O).max()), np.abs(G - O).max()
