@@ -24,6 +24,10 @@ Problem descriptions are plain dicts (see ``workloads.py``):
                for k in powers (Sec. 1, Eq. nonlinear_new; Example 5); kinds
                "gauss_over_t" exp(-sum w_i (x_i - m_i)^2) / (t + t0), params (w0, w1, w2, m0, m1, m2, t0),
                and "gauss" exp(-sum w_i (x_i - m_i)^2), params (w0, w1, w2, m0, m1, m2)
+    sde        optional (steps, beta, kappa, s, r): paths of dX_i = (beta_i - kappa_i X_i) dt
+               + (s_i + r_i X_i) dW_i by Euler-Maruyama, `steps` equal steps per segment
+               (D is then unused); u0 kind "quadratic" (c0, l_0, l_1, l_2, q_0, q_1, q_2):
+               c0 + sum_i (l_i x_i + q_i x_i^2)
 """
 from __future__ import annotations
 
@@ -45,7 +49,7 @@ STATUS_PADE_POLE_NEAR = 2
 STATUS_SERIES_PARTIAL = 4
 STATUS_HIGH_PRUNE = 8
 
-_U0_KINDS = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5}
+_U0_KINDS = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5, "quadratic": 6}
 _COEF_KINDS = {"const": 0, "gauss_over_t": 1, "gauss": 2}
 
 
@@ -66,6 +70,9 @@ class _OrProblem(ctypes.Structure):
         ("coef_kind", ctypes.c_int32),
         ("coef_param", ctypes.c_double * 8),
         ("coef_mask", ctypes.c_uint32),
+        ("sde_kind", ctypes.c_int32),
+        ("sde_steps", ctypes.c_int32),
+        ("sde_param", ctypes.c_double * 12),
     ]
 
 
@@ -140,6 +147,13 @@ def _problem(pb: dict) -> _OrProblem:
         for i, v in enumerate(params):
             s.coef_param[i] = float(v)
         s.coef_mask = sum(1 << int(k) for k in powers)
+    if "sde" in pb:
+        steps, beta, kappa, sd, rr = pb["sde"]
+        s.sde_kind = 1
+        s.sde_steps = int(steps)
+        for blk, vals in enumerate((beta, kappa, sd, rr)):
+            for i, v in enumerate(vals):
+                s.sde_param[3 * blk + i] = float(v)
     return s
 
 

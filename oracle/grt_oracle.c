@@ -41,6 +41,10 @@
  *             (Sec. 2.1 end, Sec. 2.4), after an eps-rescaling that leaves
  *             the approximant unchanged.
  *   Errors    per-order standard errors (Sec. 2.4, Eq. simplecase_discrete).
+ *   General drift and diffusion  L = sum_i (s_i + r_i x_i)^2 / 2 d_ii + (beta_i -
+ *             kappa_i x_i) d_i: the segments follow the SDE by Euler-Maruyama
+ *             with a fixed number of equal steps per segment (Eqs. SDE, green;
+ *             Sec. 2.4 uses the Euler scheme).
  *   Variable coefficients  c_k(x, t) = b_k gamma(x, t) for the terms of a
  *             mask (Sec. 1, Eq. nonlinear_new; Example 5): the split weight
  *             is multiplied by gamma at the split position and at the PDE
@@ -93,10 +97,13 @@ typedef struct {
     int32_t coef_kind; /* variable coefficients: 0 none, 1 gauss / (t + t0), 2 gauss */
     double coef_param[8];
     uint32_t coef_mask; /* bit k: c_k(x, t) = b_k gamma(x, t) */
+    int32_t sde_kind;   /* 0: L = D Lap, exact Gaussian segments; 1: Euler-Maruyama (below) */
+    int32_t sde_steps;  /* Euler steps per segment (sde_kind 1) */
+    double sde_param[12]; /* beta[3], kappa[3], s[3], r[3] */
 } or_problem;
 
 enum { OR_U0_CONST = 0, OR_U0_GAUSS = 1, OR_U0_COS_PROD = 2, OR_U0_TANH_PROD = 3, OR_U0_LOGISTIC = 4,
-       OR_U0_GAUSS_AXES = 5 };
+       OR_U0_GAUSS_AXES = 5, OR_U0_QUADRATIC = 6 };
 enum { OR_STRAT_A = 0, OR_STRAT_B = 1 };
 enum { OR_COEF_CONST = 0, OR_COEF_GAUSS_OVER_T = 1, OR_COEF_GAUSS = 2 };
 
@@ -170,6 +177,8 @@ static int or_build_setup(const or_problem *pb, or_setup *s)
     if (pb->f_deg < 0 || pb->f_deg > OR_MAX_DEG) return -1;
     if (!(pb->D >= 0.0)) return -1;
     if (pb->coef_kind < OR_COEF_CONST || pb->coef_kind > OR_COEF_GAUSS) return -1;
+    if (pb->sde_kind < 0 || pb->sde_kind > 1) return -1;
+    if (pb->sde_kind == 1 && (pb->sde_steps < 1 || pb->sde_steps > 4096)) return -1;
     if (pb->coef_kind == OR_COEF_GAUSS_OVER_T && !(pb->coef_param[6] > 0.0)) return -1;
     /* A variable linear coefficient cannot be combined with a pulled-out
      * constant potential: F's linear coefficient b_1 gamma + c is not b gamma. */
@@ -283,6 +292,11 @@ static double or_u0(const or_problem *pb, const double *x)
     }
     case OR_U0_LOGISTIC: /* a0 + a1 / (1 + exp(-(x_0 - a2) / a3)) */
         return a[0] + a[1] / (1.0 + exp(-(x[0] - a[2]) / a[3]));
+    case OR_U0_QUADRATIC: { /* a0 + sum_i (a[1+i] x_i + a[4+i] x_i^2) */
+        double v = a[0];
+        for (int i = 0; i < d; ++i) v += a[1 + i] * x[i] + a[4 + i] * x[i] * x[i];
+        return v;
+    }
     case OR_U0_GAUSS_AXES: { /* a0 + a1 exp(-sum_i a[2+i] (x_i - a[5+i])^2) */
         double r = 0.0;
         for (int i = 0; i < d; ++i) {
@@ -335,6 +349,42 @@ static void or_hash_code(or_tree *T, uint64_t code)
     T->hash *= 0x100000001B3ull;
 }
 
+/* Euler-Maruyama for dX_i = (beta_i - kappa_i X_i) dt + (s_i + r_i X_i) dW_i over a
+ * segment of length s_seg (Eqs. SDE, green: the paths of a general operator L
+ * = a_ij d_i d_j + b_i d_i with sigma^2 = a, simulated by the Euler scheme as
+ * in Sec. 2.4).  A fixed number m = sde_steps of equal steps h = s_seg / m.
+ * Step j draws from its own Philox key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1)
+ * 0x6C8E9CF5) at the node's counter with the sub bit set; its normals are
+ * Box-Muller on (w0, w1): n0 = r cos(2 pi U1), n1 = r sin(2 pi U1), and for
+ * d = 3 n2 = sqrt(-2 ln U2) cos(2 pi U3). */
+static void or_euler_segment(const or_tree *T, const or_problem *pb, const double *x, double s_seg, uint64_t id,
+                             double *y)
+{
+    const double *beta = pb->sde_param, *kappa = pb->sde_param + 3, *sd = pb->sde_param + 6,
+                 *rr = pb->sde_param + 9;
+    int d = pb->dim;
+    int m = pb->sde_steps;
+    double h = s_seg / (double)m, sh = sqrt(h);
+    for (int i = 0; i < d; ++i) y[i] = x[i];
+    for (int j = 0; j < m; ++j) {
+        uint32_t jj = (uint32_t)(j + 1);
+        uint32_t key[2] = { T->key[0] ^ (jj * 0x2545F491u), T->key[1] ^ (jj * 0x6C8E9CF5u) };
+        uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32), T->tree | 0x80000000u, T->point };
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        double z[3];
+        double r0 = sqrt(-2.0 * log(oracle_uniform(w[0])));
+        double a0 = 2.0 * M_PI * oracle_uniform(w[1]);
+        z[0] = r0 * cos(a0);
+        z[1] = r0 * sin(a0);
+        z[2] = sqrt(-2.0 * log(oracle_uniform(w[2]))) * cos(2.0 * M_PI * oracle_uniform(w[3]));
+        for (int i = 0; i < d; ++i) {
+            double X = y[i];
+            y[i] = X + (beta[i] - kappa[i] * X) * h + (sd[i] + rr[i] * X) * sh * z[i];
+        }
+    }
+}
+
 static void or_visit(or_tree *T, const double *x, double tau, uint64_t id)
 {
     const or_setup *s = T->s;
@@ -385,7 +435,8 @@ static void or_visit(or_tree *T, const double *x, double tau, uint64_t id)
         leaf = (S >= tau) || (s->ncat == 0);
         if (leaf) {
             s_seg = tau;
-            factor = exp((pb->lambda - pb->c_pot) * tau);
+            /* With no term (f = 0, hence c = 0) there is no clock: u = E[g], weight g. */
+            factor = (s->ncat == 0) ? 1.0 : exp((pb->lambda - pb->c_pot) * tau);
         } else {
             cat = or_draw_category(s, w[1]);
             s_seg = S;
@@ -395,8 +446,12 @@ static void or_visit(or_tree *T, const double *x, double tau, uint64_t id)
     }
 
     double y[OR_MAX_DIM];
-    double sc = sqrt(2.0 * pb->D * s_seg);
-    for (int i = 0; i < d; ++i) y[i] = x[i] + sc * n[i];
+    if (pb->sde_kind == 1) {
+        or_euler_segment(T, pb, x, s_seg, id, y);
+    } else {
+        double sc = sqrt(2.0 * pb->D * s_seg);
+        for (int i = 0; i < d; ++i) y[i] = x[i] + sc * n[i];
+    }
 
     if (leaf) {
         or_hash_code(T, 0);

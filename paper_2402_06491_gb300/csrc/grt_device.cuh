@@ -341,8 +341,9 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     if (STRAT == kStratB) {
       o.factor = Scalars<Real>::leaf(p) * g;
     } else {
+      // with no term (f = 0, hence c = 0) there is no clock: the leaf carries g alone
       const Real lmc = Scalars<Real>::lam_minus_c(p);
-      o.factor = (lmc == Real(0)) ? g : F::exp_scaled(lmc * tau) * g;
+      o.factor = (lmc == Real(0) || p.nterms == 0) ? g : F::exp_scaled(lmc * tau) * g;
     }
   } else {
     const Real tf = s_factor[o.cat];
