@@ -642,6 +642,10 @@ def gpu_arm(args) -> int:
                 "3-D u_t = 0.1 Lap u + u - u^3, u0 = prod tanh(x_i - 2), 9 interior planes x 32^2 nodes of the "
                 "4x4x4 split of [0,4]^3, t = 1, 1e5 trees per point (9.2e8 trees), K = 12, [6/6]")),
             "pdd_3d_pipeline": pdd_bench(grt, local, 3),
+            "drift_2d": dict(workload_bench(grt, local, "drift_2d", 10), description=(
+                "general drift and diffusion: u_t = sum_i (s_i^2/2) d_ii u - kappa_i x_i d_i u + u^2 - u, kappa = (1, 0.5), "
+                "s = (1, 0.7) (OU paths by Euler-Maruyama, 8 steps per segment), u0 = exp(-|x - (0.5,-0.3)|^2/1.28), "
+                "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, K = 8, [4/4]")),
             "var_coef_2d": dict(workload_bench(grt, local, "var_coef_2d", 10), description=(
                 "Example 5: 2-D u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (variable coefficient), u0 = e^{-x^2/4}/sqrt(4 pi), "
                 "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, binary trees q = 2/3, K = 8, [4/4]")),

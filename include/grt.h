@@ -77,6 +77,19 @@ extern "C" {
 #define GRT_U0_TANH_PROD 3 /* p0 + p1 prod_i tanh(x_i - p[2+i])               */
 #define GRT_U0_LOGISTIC 4  /* p0 + p1 / (1 + exp(-(x_0 - p2) / p3))           */
 #define GRT_U0_GAUSS_AXES 5 /* p0 + p1 exp(-sum_i p_{2+i} (x_i - p_{5+i})^2)  */
+#define GRT_U0_QUADRATIC 6  /* p0 + sum_i (p_{1+i} x_i + p_{4+i} x_i^2)        */
+
+/* Path law of a segment (Eqs. green, SDE: L = a_ij d_i d_j + b_i d_i, sigma^2 = a).
+ * GRT_SDE_HEAT: L = D Lap, each segment one exact Gaussian increment of
+ * variance 2 D s per axis.  GRT_SDE_AFFINE: per axis
+ *   dX_i = (beta_i - kappa_i X_i) dt + (s_i + r_i X_i) dW_i,
+ * sde_param = {beta[3], kappa[3], s[3], r[3]}, D unused, by Euler-Maruyama
+ * (the Euler scheme of Sec. 2.4) with sde_steps equal steps per segment;
+ * step j of a node draws one Philox4x32-10 block at the node's counter with
+ * the sub bit set under the key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1) 0x6C8E9CF5),
+ * normals by Box-Muller on (w0, w1) and, for d = 3, (w2, w3). */
+#define GRT_SDE_HEAT 0
+#define GRT_SDE_AFFINE 1
 
 /* Variable coefficients c_k(x, t) = b_k gamma(x, t) of the terms selected by
  * coef_mask (Sec. 1, Eq. nonlinear_new; Example 5 uses -e^{-x^2}/(t + 0.1) u^2).
@@ -111,6 +124,9 @@ typedef struct grt_problem {
     int32_t coef_kind;                 /* GRT_COEF_*; Strategy A rejects a variable linear    */
     double coef_param[8];              /*   term (mask bit 1) together with c_pot != 0        */
     uint32_t coef_mask;                /* bit k: c_k(x, t) = b_k gamma(x, t), k <= f_deg      */
+    int32_t sde_kind;                  /* GRT_SDE_*                                           */
+    int32_t sde_steps;                 /* AFFINE: Euler steps per segment, 1..4096            */
+    double sde_param[12];              /* AFFINE: beta[3], kappa[3], s[3], r[3]               */
 } grt_problem;
 
 typedef struct grt_ctx grt_ctx;

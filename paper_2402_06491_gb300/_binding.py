@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP, EAGAIN = 0, -1, -2, -3, -4, -5, 
 STRATEGY = {"A": 0, "B": 1}
 ARITY_LAW = {"uniform": 0, "abs": 1}
 PRECISION = {"fp32": 0, "fp64": 1}
-U0_KIND = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5}
+U0_KIND = {"const": 0, "gauss": 1, "cos_prod": 2, "tanh_prod": 3, "logistic": 4, "gauss_axes": 5, "quadratic": 6}
 COEF_KIND = {"const": 0, "gauss_over_t": 1, "gauss": 2}
 STATUS_PADE_SINGULAR, STATUS_PADE_POLE_NEAR, STATUS_SERIES_PARTIAL, STATUS_HIGH_PRUNE = 1, 2, 4, 8
 
@@ -51,6 +51,9 @@ class grt_problem(ctypes.Structure):
         ("coef_kind", ctypes.c_int32),
         ("coef_param", ctypes.c_double * 8),
         ("coef_mask", ctypes.c_uint32),
+        ("sde_kind", ctypes.c_int32),
+        ("sde_steps", ctypes.c_int32),
+        ("sde_param", ctypes.c_double * 12),
     ]
 
 
@@ -164,6 +167,13 @@ def problem_struct(pb: dict) -> grt_problem:
         for i, v in enumerate(params):
             s.coef_param[i] = float(v)
         s.coef_mask = sum(1 << int(k) for k in powers)
+    if "sde" in pb:
+        steps, beta, kappa, sd, rr = pb["sde"]
+        s.sde_kind = 1
+        s.sde_steps = int(steps)
+        for blk, vals in enumerate((beta, kappa, sd, rr)):
+            for i, v in enumerate(vals):
+                s.sde_param[3 * blk + i] = float(v)
     return s
 
 

@@ -87,7 +87,13 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
   if (pb.f_deg < 0 || pb.f_deg > GRT_MAX_DEG) return why = "f_deg must be in [0, 15]", GRT_EINVAL;
   for (int k = 0; k <= pb.f_deg; ++k)
     if (!is_finite(pb.f_coef[k])) return why = "f_coef must be finite", GRT_EINVAL;
-  if (pb.u0_kind < GRT_U0_CONST || pb.u0_kind > GRT_U0_GAUSS_AXES) return why = "unknown u0_kind", GRT_EINVAL;
+  if (pb.u0_kind < GRT_U0_CONST || pb.u0_kind > GRT_U0_QUADRATIC) return why = "unknown u0_kind", GRT_EINVAL;
+  if (pb.sde_kind != GRT_SDE_HEAT && pb.sde_kind != GRT_SDE_AFFINE) return why = "unknown sde_kind", GRT_EINVAL;
+  if (pb.sde_kind == GRT_SDE_AFFINE) {
+    if (pb.sde_steps < 1 || pb.sde_steps > 4096) return why = "sde_steps must be in [1, 4096]", GRT_EINVAL;
+    for (int i = 0; i < 12; ++i)
+      if (!is_finite(pb.sde_param[i])) return why = "sde_param must be finite", GRT_EINVAL;
+  }
   for (int i = 0; i < 8; ++i)
     if (!is_finite(pb.u0_param[i])) return why = "u0_param must be finite", GRT_EINVAL;
   if (pb.u0_kind == GRT_U0_GAUSS && pb.u0_param[2] == 0.0) return why = "GAUSS width p2 must be nonzero", GRT_EINVAL;
@@ -135,6 +141,12 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
     w.cwf[i] = (float)(w.cwd[i] * 1.4426950408889634);
   }
   w.ct0d = varcoef ? pb.coef_param[6] : 0.0;
+  w.sde_kind = pb.sde_kind;
+  w.sde_steps = pb.sde_kind == GRT_SDE_AFFINE ? pb.sde_steps : 0;
+  for (int i = 0; i < 12; ++i) {
+    w.sded[i] = pb.sde_kind == GRT_SDE_AFFINE ? pb.sde_param[i] : 0.0;
+    w.sdef[i] = (float)w.sded[i];
+  }
   w.ct0f = (float)w.ct0d;
   if (varcoef)
     for (int i = 0; i < nt; ++i)
@@ -228,6 +240,9 @@ int build_tables(const grt_problem &pb, grt::WalkParams &w, std::string &why) {
       c[2 + i] = -a[2 + i];
       c[5 + i] = a[5 + i];
     }
+    break;
+  case GRT_U0_QUADRATIC:
+    for (int i = 1; i < 7; ++i) c[i] = a[i];
     break;
   default:
     break;

@@ -19,7 +19,9 @@ constexpr int kFinThreads = 128;  // threads of a finalize (binning) block
 constexpr int kBinChunk = 8192;   // tree records binned by one finalize block
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4, kU0GaussAxes = 5 };
+enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4, kU0GaussAxes = 5,
+             kU0Quadratic = 6 };
+enum : int { kSdeHeat = 0, kSdeAffine = 1 };
 enum : int { kCoefConst = 0, kCoefGaussOverT = 1, kCoefGauss = 2 };
 enum : int { kStratA = 0, kStratB = 1 };
 
@@ -48,6 +50,11 @@ struct WalkParams {
   uint32_t coef_cat_mask;
   double cwd[3], cmd[3], ct0d;  // -w_i, centre m_i, t0
   float cwf[3], ct0f;           // -w_i log2 e, t0
+  // path law: kSdeHeat (exact Gaussian segments) or kSdeAffine (Euler-Maruyama,
+  // sde_steps steps per segment, per-axis beta, kappa, s, r)
+  int sde_kind, sde_steps;
+  double sded[12];
+  float sdef[12];
   // Philox round keys: round r uses (k0 + r W0, k1 + r W1)
   uint32_t rk0[10], rk1[10];
   uint32_t point_base;
@@ -80,6 +87,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk0)[10
     const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
     c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r],
                    (uint32_t)p0);
+  }
+  return c;
+}
+
+// The same generator under a key given at the call (round keys formed on the fly).
+__device__ __forceinline__ uint4 philox4x32_10_key(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
   }
   return c;
 }
@@ -161,6 +181,7 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
     case kU0TanhProd: b = xp[i] - p.u0d[2 + i]; break;
     case kU0Logistic: b = i == 0 ? xp[0] - p.u0d[2] : 0.0; break;
     case kU0GaussAxes: b = xp[i] - p.u0d[5 + i]; break;
+    case kU0Quadratic: b = xp[i]; break;
     case kU0CosProd: b = remainder(p.u0d[2 + i] * xp[i], 6.283185307179586476925286766559); break;
     default: break;
     }
@@ -175,6 +196,7 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
 //   TANH_PROD c0, A, s0, s1, s2
 //   LOGISTIC  c0, A, x0, -1/width
 //   GAUSS_AXES c0, A, -w0, -w1, -w2, m0, m1, m2
+//   QUADRATIC  c0, l0, l1, l2, q0, q1, q2
 template <typename Real, int DIM>
 __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&base)[DIM], const Real (&D)[DIM]) {
   using M = Math<Real>;
@@ -203,6 +225,15 @@ __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&b
   }
   case kU0Logistic:
     return c0 + A / (Real(1) + Node<Real>::exp_scaled((base[0] + D[0]) * pconst<Real>(p, 3)));
+  case kU0Quadratic: {
+    Real v = c0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const Real e = base[i] + D[i];
+      v += (pconst<Real>(p, 1 + i) + pconst<Real>(p, 4 + i) * e) * e;
+    }
+    return v;
+  }
   case kU0GaussAxes: {
     Real r = Real(0);
 #pragma unroll
@@ -261,6 +292,47 @@ template <> struct Scalars<double> {
   static __device__ __forceinline__ double lam_minus_c(const WalkParams &p) { return p.lam_minus_c; }
 };
 
+template <typename Real> __device__ __forceinline__ Real sdeconst(const WalkParams &p, int i);
+template <> __device__ __forceinline__ float sdeconst<float>(const WalkParams &p, int i) { return p.sdef[i]; }
+template <> __device__ __forceinline__ double sdeconst<double>(const WalkParams &p, int i) { return p.sded[i]; }
+
+// Euler-Maruyama over a segment of length seg for dX_i = (beta_i - kappa_i X_i) dt
+// + (s_i + r_i X_i) dW_i (the Euler scheme of Sec. 2.4 for the SDE of a general
+// operator), sde_steps equal steps.  The walk carries displacements y from the
+// root; X = x_p + y.  Step j: one Philox block at the node's counter with the
+// sub bit set, under the key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1) 0x6C8E9CF5).
+template <typename Real, int DIM>
+__device__ __forceinline__ void euler_segment(const WalkParams &p, const double *__restrict__ xp, Real seg,
+                                              uint32_t id_lo, uint32_t id_hi, uint32_t tree, uint32_t point,
+                                              Real (&y)[DIM]) {
+  using F = Node<Real>;
+  const int m = p.sde_steps;
+  const Real h = seg / (Real)m;
+  const Real sh = F::sqrt_pos(h);
+  Real x0[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) x0[i] = (Real)xp[i];
+  const uint32_t k0 = p.rk0[0], k1 = p.rk1[0];
+  for (int j = 0; j < m; ++j) {
+    const uint32_t jj = (uint32_t)(j + 1);
+    const uint4 w = philox4x32_10_key(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), k0 ^ (jj * 0x2545F491u),
+                                      k1 ^ (jj * 0x6C8E9CF5u));
+    Real z[3];
+    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.x)));
+    Real sn, cs;
+    F::sincos2pi(uniform01<Real>(w.y), &sn, &cs);
+    z[0] = r * cs;
+    z[1] = r * sn;
+    z[2] = DIM == 3 ? F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z))) * F::cos2pi(uniform01<Real>(w.w)) : Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const Real X = x0[i] + y[i];
+      y[i] += (sdeconst<Real>(p, i) - sdeconst<Real>(p, 3 + i) * X) * h +
+              (sdeconst<Real>(p, 6 + i) + sdeconst<Real>(p, 9 + i) * X) * sh * z[i];
+    }
+  }
+}
+
 // Index of the first category whose threshold exceeds w among the finite
 // thresholds thr[first .. count-1] (the last category's threshold is 2^32 and
 // is not stored): an early-exit scan, since the first categories carry most
@@ -292,7 +364,7 @@ template <typename Real, int DIM> struct NodeOut {
 // `s_factor`, `s_thr` and the caller's arity table are block-shared copies of the tables;
 // x is the displacement from the tree's root, `base` the root's shifted origin
 // and xp the root's coordinates (read only by a variable coefficient).
-template <typename Real, int DIM, int STRAT>
+template <typename Real, int DIM, int STRAT, int PATH = kSdeHeat>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
                                           const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
                                           const double *__restrict__ xp, const Real (&x)[DIM], Real tau,
@@ -332,9 +404,15 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     o.tau_c = tau - S;
     o.cat = leaf ? -1 : categorical(s_thr, w.y, 0, p.ncat_thr);
   }
-  const Real sc = F::sqrt_pos(Scalars<Real>::two_D(p) * seg);
+  if constexpr (PATH == kSdeAffine) {
 #pragma unroll
-  for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
+    for (int i = 0; i < DIM; ++i) o.y[i] = x[i];
+    euler_segment<Real, DIM>(p, xp, seg, id_lo, id_hi, tree, point, o.y);
+  } else {
+    const Real sc = F::sqrt_pos(Scalars<Real>::two_D(p) * seg);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
+  }
 
   if (leaf) {
     const Real g = initial_data<Real, DIM>(p, base, o.y);

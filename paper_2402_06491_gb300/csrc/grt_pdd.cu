@@ -541,6 +541,8 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   if (!c) return GRT_EINVAL;
   int rc = check_grid(c, g);
   if (rc != GRT_OK) return rc;
+  if (c->pb.sde_kind != GRT_SDE_HEAT)
+    return c->set_error(GRT_ENOTSUP, "the PDD local solver discretises D Lap: paths must be GRT_SDE_HEAT");
   if (!d_u_nodes || !d_u_out) return c->set_error(GRT_EINVAL, "u_nodes and u_out must be non-NULL");
   const int d = g->dim;
   cudaStream_t s = (cudaStream_t)stream;  // NULL: the legacy default stream, as for the solves

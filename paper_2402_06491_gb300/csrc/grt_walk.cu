@@ -54,7 +54,7 @@ __device__ __forceinline__ int find_point(const uint32_t *__restrict__ prefix, i
   return lo;
 }
 
-template <typename Real, int DIM, int STRAT, int WARPS, int SLEV>
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int PATH = kSdeHeat>
 __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Real s_factor[kMaxTerms];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
     // pending sibling from the stack (up), or the tree is done.
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, p.x + (size_t)pidx * DIM, x, tau, id_lo, id_hi, tree,
+    node_step<Real, DIM, STRAT, PATH>(p, s_factor, s_thr, base, p.x + (size_t)pidx * DIM, x, tau, id_lo, id_hi, tree,
                                 point, o);
     W *= o.factor;
     const bool split = o.cat >= 0;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
 }
 
 // One thread per tree: per-tree records (diagnostic form of the same streams).
-template <typename Real, int DIM, int STRAT>
+template <typename Real, int DIM, int STRAT, int PATH>
 __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, double x0_2, Real t0, uint32_t point,
                              uint32_t first_tree, uint32_t ntrees, int32_t *order, double *wout, uint32_t *nodes_out,
                              uint64_t *hash_out) {
@@ -282,7 +282,7 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
   for (;;) {
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT>(p, s_factor, s_thr, base, xin, x, tau, (uint32_t)id, (uint32_t)(id >> 32), tree,
+    node_step<Real, DIM, STRAT, PATH>(p, s_factor, s_thr, base, xin, x, tau, (uint32_t)id, (uint32_t)(id >> 32), tree,
                                 point, o);
     h = (h ^ (uint64_t)(o.cat + 1)) * 0x100000001B3ull;
     W *= o.factor;
@@ -330,10 +330,10 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-template <typename Real, int DIM, int STRAT, int WARPS, int SLEV>
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int PATH = kSdeHeat>
 static cudaError_t launch_walk_t(const WalkParams &p, const WalkConfig &cfg, int num_sms, cudaStream_t stream) {
   const size_t smem = warp_stack_bytes<Real, DIM>(p.K, SLEV) * WARPS;
-  auto kern = walk_kernel<Real, DIM, STRAT, WARPS, SLEV>;
+  auto kern = walk_kernel<Real, DIM, STRAT, WARPS, SLEV, PATH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -351,6 +351,8 @@ static cudaError_t launch_walk_t(const WalkParams &p, const WalkConfig &cfg, int
 
 template <typename Real, int DIM, int STRAT>
 static cudaError_t launch_walk_cfg(const WalkParams &p, const WalkConfig &cfg, int num_sms, cudaStream_t stream) {
+  // Euler paths: one instantiation (4 warps, stack in shared memory); blocks per SM and tile still apply
+  if (p.sde_kind == kSdeAffine) return launch_walk_t<Real, DIM, STRAT, 4, 0, kSdeAffine>(p, cfg, num_sms, stream);
   if (cfg.warps == 8 && cfg.smem_levels == 3) return launch_walk_t<Real, DIM, STRAT, 8, 3>(p, cfg, num_sms, stream);
   if (cfg.warps == 8) return launch_walk_t<Real, DIM, STRAT, 8, 0>(p, cfg, num_sms, stream);
   if (cfg.smem_levels == 3) return launch_walk_t<Real, DIM, STRAT, 4, 3>(p, cfg, num_sms, stream);
@@ -363,6 +365,15 @@ cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, c
   if (dim == D && strategy == S) return launch_walk_cfg<R, D, S>(p, cfg, num_sms, stream);
   if (fp64) {  // the FP64 walk runs in the default configuration
     const WalkConfig dflt{};
+    if (p.sde_kind == kSdeAffine) {
+      if (dim == 1 && strategy == kStratA) return launch_walk_t<double, 1, kStratA, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      if (dim == 2 && strategy == kStratA) return launch_walk_t<double, 2, kStratA, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      if (dim == 3 && strategy == kStratA) return launch_walk_t<double, 3, kStratA, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      if (dim == 1 && strategy == kStratB) return launch_walk_t<double, 1, kStratB, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      if (dim == 2 && strategy == kStratB) return launch_walk_t<double, 2, kStratB, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      if (dim == 3 && strategy == kStratB) return launch_walk_t<double, 3, kStratB, 4, 0, kSdeAffine>(p, dflt, num_sms, stream);
+      return cudaErrorInvalidValue;
+    }
     if (dim == 1 && strategy == kStratA) return launch_walk_t<double, 1, kStratA, 4, 0>(p, dflt, num_sms, stream);
     if (dim == 2 && strategy == kStratA) return launch_walk_t<double, 2, kStratA, 4, 0>(p, dflt, num_sms, stream);
     if (dim == 3 && strategy == kStratA) return launch_walk_t<double, 3, kStratA, 4, 0>(p, dflt, num_sms, stream);
@@ -384,8 +395,12 @@ static cudaError_t launch_trees_t(const WalkParams &p, const double *x0, double 
   const unsigned threads = 128;
   const unsigned blocks = (ntrees + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
-  trees_kernel<Real, DIM, STRAT><<<blocks, threads, 0, stream>>>(
-      p, x0[0], DIM > 1 ? x0[1] : 0.0, DIM > 2 ? x0[2] : 0.0, (Real)t0, point, first, ntrees, order, w, nodes, hash);
+  if (p.sde_kind == kSdeAffine)
+    trees_kernel<Real, DIM, STRAT, kSdeAffine><<<blocks, threads, 0, stream>>>(
+        p, x0[0], DIM > 1 ? x0[1] : 0.0, DIM > 2 ? x0[2] : 0.0, (Real)t0, point, first, ntrees, order, w, nodes, hash);
+  else
+    trees_kernel<Real, DIM, STRAT, kSdeHeat><<<blocks, threads, 0, stream>>>(
+        p, x0[0], DIM > 1 ? x0[1] : 0.0, DIM > 2 ? x0[2] : 0.0, (Real)t0, point, first, ntrees, order, w, nodes, hash);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,9 @@ def test_library_is_the_in_tree_build(lib):
 @pytest.mark.parametrize("field,value,needle", [
     ("dim", 4, "dim"), ("D", -1.0, "D must"), ("q", 1.0, "0 < q < 1"), ("q", 0.0, "0 < q < 1"),
     ("strategy", "C", None), ("u0", ("gauss", (0.0, 1.0, 0.0)), "width"),
+    ("coef", ("gauss_over_t", (1, 0, 0, 0, 0, 0, 0.0), [2]), "t0"),
+    ("sde", (0, (0.0, 0.0), (0.0, 0.0), (1.0, 1.0), (0.0, 0.0)), "sde_steps"),
+    ("sde", (5000, (0.0, 0.0), (0.0, 0.0), (1.0, 1.0), (0.0, 0.0)), "sde_steps"),
 ])
 def test_invalid_problems_are_rejected_before_any_device_call(lib, field, value, needle):
     import paper_2402_06491_gb300 as pkg

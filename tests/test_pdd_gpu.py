@@ -82,6 +82,15 @@ def test_pdd_solve_parity(grt, torch, dim, sub, cells, nodes):
     assert np.allclose(G, O, rtol=0, atol=1e-10 * np.abs(O).max()), np.abs(G - O).max()
 
 
+def test_pdd_needs_heat_paths(grt):
+    ctx = grt.grt_create(workloads.problem_drift_2d(), 0)
+    g = dict(dim=2, lo=[0.0, 0.0], hi=[2.0, 2.0], sub=[2, 2], cells=[4, 4], nodes=[5, 5], t_nodes=4, T=1.0, nsteps=8)
+    with pytest.raises(grt.GrtError) as ei:
+        grt.grt_pdd_solve(ctx, g, 0, 0)
+    assert ei.value.code == -5
+    ctx.close()
+
+
 def test_pdd_rejects_bad_grids(grt):
     ctx = grt.grt_create(_pdd_problem(2), 0)
     good = dict(dim=2, lo=[0.0, 0.0], hi=[2.0, 2.0], sub=[2, 2], cells=[4, 4], nodes=[5, 5], t_nodes=4, T=1.0,

@@ -18,6 +18,9 @@ probabilistic-domain-decomposition set-up (Sec. 2.4 Examples 1-3, Sec. 3):
     pdd_3d     u_t = 0.1 Lap u + u - u^3 on the 9 interior planes of a 4x4x4 split
     var_coef_2d  u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (Sec. 3 Example 5: a variable
                coefficient on the nonlinear term), u0 = e^{-x^2/4}/sqrt(4 pi), t = 0.5
+    drift_2d   u_t = L u + u^2 - u with a general operator
+               L = sum_i (s_i^2 / 2) d_ii - kappa_i x_i d_i (anisotropic Ornstein-Uhlenbeck
+               paths, Euler-Maruyama, Eqs. green and SDE), t = 0.5
 """
 from __future__ import annotations
 
@@ -82,6 +85,13 @@ def problem_var_coef_2d(strategy: str = "B", precision: str = "fp32") -> dict:
                                                                        0.25, 0.0, 0.0, 0.0, 0.0, 0.0)),
                 coef=("gauss_over_t", (1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.1), [2]), strategy=strategy, lam=1.0,
                 c_pot=0.0, q=2.0 / 3.0, arity_law="uniform", precision=precision)
+
+
+def problem_drift_2d(strategy: str = "B", precision: str = "fp32", steps: int = 8) -> dict:
+    """General drift and diffusion: OU paths dX_i = -kappa_i X_i dt + s_i dW_i, kappa = (1, 0.5), s = (1, 0.7)."""
+    return dict(dim=2, D=0.0, f_coef=[0.0, -1.0, 1.0], u0=("gauss", (0.0, 1.0, 0.8, 0.5, -0.3)),
+                sde=(steps, (0.0, 0.0), (1.0, 0.5), (1.0, 0.7), (0.0, 0.0)), strategy=strategy, lam=1.0, c_pot=0.0,
+                q=default_q([0.0, -1.0, 1.0], "uniform"), arity_law="uniform", precision=precision)
 
 
 def workload_kpp_1d() -> dict:
@@ -157,12 +167,22 @@ def workload_var_coef_2d() -> dict:
                 ntrees=np.full(n, 100_000, np.uint64), K=8, L=4, M=4, seed=0)
 
 
+def workload_drift_2d() -> dict:
+    g = np.linspace(-3.0, 3.0, 16)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x = np.stack([X.ravel(), Y.ravel()], axis=1)
+    n = x.shape[0]
+    return dict(name="drift_2d", problem=problem_drift_2d(), x=x, t=np.full(n, 0.5),
+                ntrees=np.full(n, 100_000, np.uint64), K=8, L=4, M=4, seed=0)
+
+
 WORKLOADS = {
     "kpp_1d": workload_kpp_1d,
     "sin_2d": workload_sin_2d,
     "uneven_2d": workload_uneven_2d,
     "pdd_3d": workload_pdd_3d,
     "var_coef_2d": workload_var_coef_2d,
+    "drift_2d": workload_drift_2d,
 }
 
 
