@@ -50,7 +50,7 @@ def _walk_traffic():
         want = re.search(r"source_sha256_16: ([0-9a-f]+)", text).group(1)
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
         h = hashlib.sha256()
-        for f in ("grt_device.cuh", "grt_walk.cu"):
+        for f in ("grt_device.cuh", "grt_walk.cuh"):
             with open(os.path.join(ROOT, "paper_2402_06491_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
         return traffic if h.hexdigest()[:16] == want else None

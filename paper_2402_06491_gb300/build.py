@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libgrt.so")
 
-SOURCES = ["grt_api.cu", "grt_walk.cu", "grt_finalize.cu", "grt_server.cu", "grt_pdd.cu"]
+SOURCES = ["grt_api.cu", "grt_walk.cu", "grt_walk_feat.cu", "grt_trees.cu", "grt_finalize.cu", "grt_server.cu",
+           "grt_pdd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -22,6 +22,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 enum : int { kU0Const = 0, kU0Gauss = 1, kU0CosProd = 2, kU0TanhProd = 3, kU0Logistic = 4, kU0GaussAxes = 5,
              kU0Quadratic = 6 };
 enum : int { kSdeHeat = 0, kSdeAffine = 1 };
+// compile-time features of a walk instantiation
+enum : int { kFeatEuler = 1, kFeatVarCoef = 2 };
 enum : int { kCoefConst = 0, kCoefGaussOverT = 1, kCoefGauss = 2 };
 enum : int { kStratA = 0, kStratB = 1 };
 
@@ -74,6 +76,11 @@ struct WalkParams {
   unsigned long long *stats; // [0] nodes visited (added by the walk)
   uint32_t *counter;         // work-queue head
 };
+
+// The compile-time features a problem needs (Euler paths, variable coefficients).
+__host__ __device__ inline int walk_features(const WalkParams &p) {
+  return (p.sde_kind == kSdeAffine ? kFeatEuler : 0) | (p.coef_kind != kCoefConst ? kFeatVarCoef : 0);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each round multiplies
@@ -140,22 +147,63 @@ template <> struct Math<double> {
 // its accuracy holds on the argument range:
 //   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ, ~2 ulp)
 //   e^v           = 2^(v log2 e), the log2 e folded into the caller's constant
-// ln U and sin / cos of 2 pi U use the accurate library functions: the SFU's
-// absolute error (~2^-22) becomes a large relative error of -2 ln U for U
-// near 1 and of the normals, which shows up in u0 near its zeros.  The FP64
-// walk uses the library functions throughout.
+// ln U uses the accurate library function and sin / cos of 2 pi U an octant
+// reduction on the bits of the Philox word with short Taylor polynomials: the
+// SFU's absolute error (~2^-22) would become a large relative error of -2 ln U
+// for U near 1 and of the normals, which shows up in u0 near its zeros.  The
+// FP64 walk uses the library functions throughout.
 template <typename Real> struct Node;
 template <> struct Node<float> {
   static __device__ __forceinline__ float neg2ln(float u) { return -2.0f * logf(u); }
-  static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
-  static __device__ __forceinline__ float cos2pi(float u) { return cospif(2.0f * u); }
+  // sin and cos of 2 pi U(w) from the bits of w: the top three bits pick the
+  // octant, the next twenty the offset in it, so no floating-point range
+  // reduction is needed.  With o = w >> 29 and rr the 20-bit offset (mirrored
+  // in odd octants), phi = (rr + 1/2) 2^-20 pi/4 is in (0, pi/4), where
+  // sin phi = phi - phi^3/3! + ... - phi^9/9! and cos phi = 1 - phi^2/2! + ... -
+  // phi^10/10! truncate below 3e-9 relative; the octant's symmetries then swap
+  // and sign the pair (bit 29 ^ bit 30: swap; bit 31: sign of sin; bit 31 ^
+  // bit 30: sign of cos).  Within 2 ulp of the exact values.
+  static __device__ __forceinline__ void sincos_phi(uint32_t w, float *sp, float *cp) {
+    const uint32_t hmask = (uint32_t)((int32_t)(w << 2) >> 31);
+    const uint32_t rr = ((w >> 9) ^ hmask) & 0xFFFFFu;
+    const float v = __fsub_rn(__uint_as_float(0x3F800004u | (rr << 3)), 1.0f);  // (rr + 1/2) 2^-20, exact
+    const float phi = v * 0.785398163397448309616f;
+    const float p2 = phi * phi;
+    float ps = fmaf(p2, 2.75573192239858906526e-6f, -1.98412698412698412698e-4f);
+    ps = fmaf(p2, ps, 8.33333333333333333333e-3f);
+    ps = fmaf(p2, ps, -1.66666666666666666667e-1f);
+    *sp = fmaf(p2 * phi, ps, phi);
+    float pc = fmaf(p2, -2.75573192239858906526e-7f, 2.48015873015873015873e-5f);
+    pc = fmaf(p2, pc, -1.38888888888888888889e-3f);
+    pc = fmaf(p2, pc, 4.16666666666666666667e-2f);
+    pc = fmaf(p2, pc, -0.5f);
+    *cp = fmaf(p2, pc, 1.0f);
+  }
+  static __device__ __forceinline__ void sincos2pi_w(uint32_t w, float *s, float *c) {
+    float sp, cp;
+    sincos_phi(w, &sp, &cp);
+    const uint32_t t = w ^ (w << 1);
+    const bool swap = (t >> 30) & 1u;
+    const float a = swap ? cp : sp, b = swap ? sp : cp;
+    *s = __uint_as_float(__float_as_uint(a) ^ (w & 0x80000000u));
+    *c = __uint_as_float(__float_as_uint(b) ^ (t & 0x80000000u));
+  }
+  static __device__ __forceinline__ float cos2pi_w(uint32_t w) {
+    float sp, cp;
+    sincos_phi(w, &sp, &cp);
+    const uint32_t t = w ^ (w << 1);
+    const float b = ((t >> 30) & 1u) ? sp : cp;
+    return __uint_as_float(__float_as_uint(b) ^ (t & 0x80000000u));
+  }
   static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
   static __device__ __forceinline__ float exp_scaled(float v) { return exp2f(v); }  // v already times log2 e
 };
 template <> struct Node<double> {
   static __device__ __forceinline__ double neg2ln(double u) { return -2.0 * ::log(u); }
-  static __device__ __forceinline__ void sincos2pi(double u, double *s, double *c) { ::sincospi(2.0 * u, s, c); }
-  static __device__ __forceinline__ double cos2pi(double u) { return ::cospi(2.0 * u); }
+  static __device__ __forceinline__ void sincos2pi_w(uint32_t w, double *s, double *c) {
+    ::sincospi(2.0 * uniform01<double>(w), s, c);
+  }
+  static __device__ __forceinline__ double cos2pi_w(uint32_t w) { return ::cospi(2.0 * uniform01<double>(w)); }
   static __device__ __forceinline__ double sqrt_pos(double v) { return ::sqrt(v); }
   static __device__ __forceinline__ double exp_scaled(double v) { return ::exp(v); }  // v is the plain exponent
 };
@@ -320,10 +368,10 @@ __device__ __forceinline__ void euler_segment(const WalkParams &p, const double 
     Real z[3];
     const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.x)));
     Real sn, cs;
-    F::sincos2pi(uniform01<Real>(w.y), &sn, &cs);
+    F::sincos2pi_w(w.y, &sn, &cs);
     z[0] = r * cs;
     z[1] = r * sn;
-    z[2] = DIM == 3 ? F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z))) * F::cos2pi(uniform01<Real>(w.w)) : Real(0);
+    z[2] = DIM == 3 ? F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z))) * F::cos2pi_w(w.w) : Real(0);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
       const Real X = x0[i] + y[i];
@@ -364,7 +412,7 @@ template <typename Real, int DIM> struct NodeOut {
 // `s_factor`, `s_thr` and the caller's arity table are block-shared copies of the tables;
 // x is the displacement from the tree's root, `base` the root's shifted origin
 // and xp the root's coordinates (read only by a variable coefficient).
-template <typename Real, int DIM, int STRAT, int PATH = kSdeHeat>
+template <typename Real, int DIM, int STRAT, int FEAT = 0>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
                                           const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
                                           const double *__restrict__ xp, const Real (&x)[DIM], Real tau,
@@ -378,14 +426,14 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   {
     const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z)));
     Real s, c;
-    F::sincos2pi(uniform01<Real>(w.w), &s, &c);
+    F::sincos2pi_w(w.w, &s, &c);
     n[0] = r * c;
     if (DIM > 1) n[DIM > 1 ? 1 : 0] = r * s;
   }
   if (DIM == 3) {
     const uint4 w2 = philox4x32_10(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), p.rk0, p.rk1);
     const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w2.x)));
-    n[DIM - 1] = r * F::cos2pi(uniform01<Real>(w2.y));
+    n[DIM - 1] = r * F::cos2pi_w(w2.y);
   }
 
   bool leaf;
@@ -404,7 +452,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     o.tau_c = tau - S;
     o.cat = leaf ? -1 : categorical(s_thr, w.y, 0, p.ncat_thr);
   }
-  if constexpr (PATH == kSdeAffine) {
+  if constexpr ((FEAT & kFeatEuler) != 0) {
 #pragma unroll
     for (int i = 0; i < DIM; ++i) o.y[i] = x[i];
     euler_segment<Real, DIM>(p, xp, seg, id_lo, id_hi, tree, point, o.y);
@@ -431,8 +479,8 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
       const Real lmc = Scalars<Real>::lam_minus_c(p);
       o.factor = (lmc == Real(0)) ? tf : F::exp_scaled(lmc * S) * tf;
     }
-    if (p.coef_kind != kCoefConst && ((p.coef_cat_mask >> o.cat) & 1u))
-      o.factor *= coef_gamma<Real, DIM>(p, xp, o.y, o.tau_c);
+    if constexpr ((FEAT & kFeatVarCoef) != 0)
+      if ((p.coef_cat_mask >> o.cat) & 1u) o.factor *= coef_gamma<Real, DIM>(p, xp, o.y, o.tau_c);
   }
 }
 

@@ -43,6 +43,8 @@ struct WalkConfig {
 
 cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms,
                         cudaStream_t stream);
+cudaError_t launch_walk_feat(bool fp64, int dim, int strategy, int feat, const WalkParams &p, const WalkConfig &cfg,
+                             int num_sms, cudaStream_t stream);
 cudaError_t launch_trees(bool fp64, int dim, int strategy, const WalkParams &p, const double *x0, double t0,
                          uint32_t point, uint32_t first, uint32_t ntrees, int32_t *order, double *w, uint32_t *nodes,
                          uint64_t *hash, cudaStream_t stream);
