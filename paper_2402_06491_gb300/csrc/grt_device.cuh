@@ -73,7 +73,7 @@ struct WalkParams {
   uint32_t total_items;      // queue chunks
   void *rec_w;               // [total trees] tree weights (float or double)
   uint8_t *rec_o;            // [total trees] tree orders (K+1 = pruned)
-  unsigned long long *stats; // [0] nodes visited (added by the walk)
+  unsigned long long *stats; // [0] nodes visited (added by the walk), [1] splits, [2] pruned trees (the binning)
   uint32_t *counter;         // work-queue head
 };
 

@@ -172,13 +172,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
     }
     s_pt = lo;
   }
-  // per-thread columns: acc[o * T + tid] = (S1, Kahan compensation of S1, S2, S|W|), cn = count
+  // per-thread columns: acc[o * T + tid] = (S1, Kahan compensation of S1, S2, S|W|) for the kept
+  // orders o = 0..K; pruned trees (order K+1, weight 0) are only counted, in a register
   Acc4<Acc> *acc = reinterpret_cast<Acc4<Acc> *>(smem);
-  uint32_t *cn = reinterpret_cast<uint32_t *>(acc + R * T);
-  for (int r = 0; r < R; ++r) {
-    acc[r * T + tid] = Acc4<Acc>{Acc(0), Acc(0), Acc(0), Acc(0)};
-    cn[r * T + tid] = 0u;
-  }
+  for (int r = 0; r <= K; ++r) acc[r * T + tid] = Acc4<Acc>{Acc(0), Acc(0), Acc(0), Acc(0)};
+  __shared__ uint32_t s_pruned[T / 32];
   __syncthreads();
   const int pt = s_pt;
   // this chunk's records [r0, r1); r0 is a multiple of 4 (4-aligned point segments, 8192-record chunks)
@@ -186,21 +184,28 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   const unsigned long long r0 = seg + (unsigned long long)(chunk - f.chunk_prefix[pt]) * kBinChunk;
   const unsigned long long r1 = min(r0 + (unsigned long long)kBinChunk, seg + f.ntrees[pt]);
   const Acc *rw = reinterpret_cast<const Acc *>(f.rec_w);
-  auto bin = [&](uint32_t o4, const Acc (&w4)[4], unsigned long long i) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (i + q >= r1) break;
-      const int o = (int)((o4 >> (8 * q)) & 0xFFu);
+  uint32_t npruned = 0, osum = 0;  // pruned trees; sum of the orders (= splits, K+1 for a pruned tree)
+  auto bin1 = [&](int o, Acc w) {
+    osum += (uint32_t)o;
+    if (o <= K) {
       const int a = o * T + tid;
-      if (o <= K) {
-        const Acc w = w4[q];
-        Acc4<Acc> v = acc[a];
-        kahan_add(v.s1, v.c1, w);
-        v.s2 += w * w;
-        v.sa += w < Acc(0) ? -w : w;
-        acc[a] = v;
-      }
-      cn[a] += 1u;
+      Acc4<Acc> v = acc[a];
+      kahan_add(v.s1, v.c1, w);
+      v.s2 += w * w;
+      v.sa += w < Acc(0) ? -w : w;
+      acc[a] = v;
+    } else {
+      ++npruned;
+    }
+  };
+  auto bin = [&](uint32_t o4, const Acc (&w4)[4], unsigned long long i) {
+    if (i + 4 <= r1) {  // a full group (every group but possibly the chunk's last)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bin1((int)((o4 >> (8 * q)) & 0xFFu), w4[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (i + q < r1) bin1((int)((o4 >> (8 * q)) & 0xFFu), w4[q]);
     }
   };
   // thread tid takes record groups r0 + 4 (tid + j T): one 32-bit load of four orders and one
@@ -227,6 +232,18 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
 #pragma unroll
     for (int q = 0; q < 4; ++q) wa[q] = wb[q];
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    npruned += __shfl_xor_sync(kFull, npruned, off);
+    osum += __shfl_xor_sync(kFull, osum, off);
+  }
+  if (lane == 0) {
+    s_pruned[warp] = npruned;
+    if (f.stats) {
+      atomicAdd(f.stats + 1, (unsigned long long)osum);
+      atomicAdd(f.stats + 2, (unsigned long long)npruned);
+    }
+  }
   __syncthreads();
   // rows in a fixed order: warp w takes rows w, w + T/32, ...; lane l adds
   // columns l, l+32, ... with compensation, then a fixed butterfly over lanes
@@ -234,15 +251,13 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   const uint32_t cfirst = f.tree_first ? f.tree_first[pt] : 0u;
   const uint32_t slot0 = f.part_slot ? f.part_slot[pt] : f.chunk_prefix[pt];
   double *part = f.part + (size_t)(slot0 + cfirst / kBinChunk + (chunk - f.chunk_prefix[pt])) * pstride;
-  for (int r = warp; r < R; r += T / 32) {
+  for (int r = warp; r <= K; r += T / 32) {
     Acc a1 = 0, k1 = 0, a2 = 0, k2 = 0, a3 = 0, k3 = 0;
-    uint32_t ac = 0;
     for (int j = lane; j < T; j += 32) {
       const Acc4<Acc> v = acc[r * T + j];
       kahan_add(a1, k1, v.s1 - v.c1);
       kahan_add(a2, k2, v.s2);
       kahan_add(a3, k3, v.sa);
-      ac += cn[r * T + j];
     }
     // butterfly in the walk's precision (FP64 arithmetic is scarce on this GPU:
     // it is used once per row, for the conversion)
@@ -252,14 +267,22 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
       d1 += __shfl_xor_sync(kFull, d1, off);
       d2 += __shfl_xor_sync(kFull, d2, off);
       d3 += __shfl_xor_sync(kFull, d3, off);
-      ac += __shfl_xor_sync(kFull, ac, off);
     }
     if (lane == 0) {
       part[r] = (double)d1;
       part[R + r] = (double)d2;
       part[2 * R + r] = (double)d3;
-      part[3 * R + r] = (double)ac;
+      part[3 * R + r] = 0.0;
     }
+  }
+  if (tid == 0) {  // the pruned row: a count only
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < T / 32; ++w) c += s_pruned[w];
+    part[K + 1] = 0.0;
+    part[R + K + 1] = 0.0;
+    part[2 * R + K + 1] = 0.0;
+    part[3 * R + K + 1] = (double)c;
   }
   // publish this chunk (its writers fence); the point's last chunk to finish completes the point
   if (lane == 0) __threadfence();
@@ -297,17 +320,12 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   __syncthreads();
   if (tid == 0) {
     const double pruned = tot[3][K + 1];
-    double splits = (double)(K + 1) * pruned;
-    for (int o = 1; o <= K; ++o) splits += (double)o * tot[3][o];
     int st = 0;
     const double u = pade_value(a, f.L, f.M, &st);
     if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
     f.u[row] = u;
     if (f.status) f.status[row] = st;
-    if (f.stats) {
-      atomicAdd(f.stats + 1, (unsigned long long)splits);
-      atomicAdd(f.stats + 2, (unsigned long long)pruned);
-    }
+
   }
 }
 
@@ -322,7 +340,7 @@ __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, doub
 }
 
 template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParams &f, cudaStream_t stream) {
-  const size_t smem = (size_t)(f.K + 2) * kFinThreads * (sizeof(Acc4<Acc>) + sizeof(uint32_t));
+  const size_t smem = (size_t)(f.K + 1) * kFinThreads * sizeof(Acc4<Acc>);
   cudaError_t e = cudaFuncSetAttribute(finalize_kernel<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   finalize_kernel<Acc><<<f.total_chunks, kFinThreads, smem, stream>>>(f);

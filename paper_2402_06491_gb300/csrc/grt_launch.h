@@ -29,8 +29,8 @@ struct FinalizeParams {
   int n, K, L, M;
   double *u;                 // [n]
   double *coef, *se;         // [n][K+1] or null
-  int32_t *status;           // [n] or null
-  unsigned long long *stats; // [1] splitting events, [2] pruned trees (added here)
+  int32_t *status;
+  unsigned long long *stats; // [1] splitting events (sum of record orders), [2] pruned trees: added here           // [n] or null
 };
 
 // Launch shape of the walk kernel (results do not depend on it).
