@@ -15,7 +15,7 @@ namespace grt {
 constexpr int kMaxTerms = 16;     // powers 0..15 of f
 constexpr int kMaxK = 16;         // highest series order
 constexpr int kTile = 512;        // default trees per work-queue chunk
-constexpr int kFinThreads = 128;  // threads of a finalize (binning) block
+constexpr int kFinThreads = 64;   // threads of a finalize (binning) block
 constexpr int kBinChunk = 8192;   // tree records binned by one finalize block
 constexpr unsigned kFull = 0xFFFFFFFFu;
 

@@ -163,14 +163,17 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   const uint32_t chunk = blockIdx.x;
   __shared__ int s_pt;
   __shared__ bool s_last;
-  if (tid == 0) {  // point owning this chunk: largest p with chunk_prefix[p] <= chunk
+  if (warp == 0) {  // point owning this chunk: largest p with chunk_prefix[p] <= chunk (32-way search)
     int lo = 0, hi = f.n;
     while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (f.chunk_prefix[mid] <= chunk) lo = mid;
-      else hi = mid;
+      const int step = (hi - lo + 31) >> 5;
+      const int idx = lo + lane * step;
+      const bool ok = (idx < hi) && (__ldg(f.chunk_prefix + idx) <= chunk);
+      const int cnt = __popc(__ballot_sync(kFull, ok));
+      lo = lo + (cnt - 1) * step;
+      hi = min(lo + step, hi);
     }
-    s_pt = lo;
+    if (lane == 0) s_pt = lo;
   }
   // per-thread columns: acc[o * T + tid] = (S1, Kahan compensation of S1, S2, S|W|) for the kept
   // orders o = 0..K; pruned trees (order K+1, weight 0) are only counted, in a register
@@ -299,12 +302,12 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizePar
   __threadfence();
   __shared__ double tot[4][kMaxK + 2];
   __shared__ double a[kMaxK + 1];
-  if (tid < 4 * R) {  // thread (stat, row) adds the point's chunk sums in chunk order
-    const double *pp = f.part + (size_t)slot0 * pstride + tid;
+  for (int e = tid; e < 4 * R; e += T) {  // entry (stat, row) adds the point's chunk sums in chunk order
+    const double *pp = f.part + (size_t)slot0 * pstride + e;
     const uint32_t nch = ntot == 0u ? 1u : (ntot + kBinChunk - 1) / kBinChunk;
     double s = 0.0, c = 0.0;
     for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
-    tot[tid / R][tid % R] = s - c;
+    tot[e / R][e % R] = s - c;
   }
   __syncthreads();
   const double N = (double)ntot;
