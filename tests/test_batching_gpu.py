@@ -36,9 +36,9 @@ def _device_case(grt, wl):
     return torch, bufs
 
 
-@pytest.mark.parametrize("name", ["uneven_2d", "pdd_3d"])
+@pytest.mark.parametrize("name", ["uneven_2d", "pdd_3d", "var_coef_2d", "drift_2d"])
 def test_every_launch_shape_gives_the_same_bits(grt, name):
-    wl = workloads.subsample(workloads.WORKLOADS[name](), 96, ntrees=20000)
+    wl = workloads.subsample(workloads.WORKLOADS[name](), 96, ntrees=20000 if name != "drift_2d" else 4000)
     torch, b = _device_case(grt, wl)
     ctx = grt.grt_create(wl["problem"], 0)
     plan = grt.grt_plan_create(ctx, wl["ntrees"], wl["K"], wl["L"], wl["M"])

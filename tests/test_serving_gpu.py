@@ -28,7 +28,8 @@ def _requests(rng):
     """A mix of problems, dimensions, series shapes, sizes and budgets (some split over many steps)."""
     specs = []
     for name, npts, lo, hi in [("sin_2d", 7, 1000, 40000), ("kpp_1d", 5, 500, 9000), ("pdd_3d", 4, 2000, 30000),
-                               ("uneven_2d", 3, 100, 70000), ("sin_2d", 1, 0, 1), ("sin_2d", 2, 8192, 8193)]:
+                               ("uneven_2d", 3, 100, 70000), ("sin_2d", 1, 0, 1), ("sin_2d", 2, 8192, 8193),
+                               ("var_coef_2d", 3, 5000, 30000), ("drift_2d", 2, 3000, 20000)]:
         wl = workloads.WORKLOADS[name]()
         idx = rng.choice(wl["x"].shape[0], size=npts, replace=False)
         nt = rng.integers(lo, hi, size=npts).astype(np.uint64)
