@@ -146,7 +146,7 @@ template <> struct Math<double> {
 // Node-body arithmetic.  The FP32 walk uses the special-function unit where
 // its accuracy holds on the argument range:
 //   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ, ~2 ulp)
-//   e^v           = 2^(v log2 e), the log2 e folded into the caller's constant
+//   e^v           = 2^(v log2 e) by ex2.approx, the log2 e folded into the caller's constant
 // ln U uses the accurate library function and sin / cos of 2 pi U an octant
 // reduction on the bits of the Philox word with short Taylor polynomials: the
 // SFU's absolute error (~2^-22) would become a large relative error of -2 ln U
@@ -196,7 +196,13 @@ template <> struct Node<float> {
     return __uint_as_float(__float_as_uint(b) ^ (t & 0x80000000u));
   }
   static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
-  static __device__ __forceinline__ float exp_scaled(float v) { return exp2f(v); }  // v already times log2 e
+  // 2^v by the PTX ex2.approx.ftz.f32 instruction (v already times log2 e; results
+  // below the normal range flush to zero, which no weight of interest reaches)
+  static __device__ __forceinline__ float exp_scaled(float v) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+  }
 };
 template <> struct Node<double> {
   static __device__ __forceinline__ double neg2ln(double u) { return -2.0 * ::log(u); }
