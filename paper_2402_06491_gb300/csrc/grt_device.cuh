@@ -446,8 +446,10 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
   Real seg, S;
   if (STRAT == kStratB) {
     // joint draw: category 0 is the leaf (w < thr[0]), category j >= 1 is term j - 1
-    leaf = p.ncat_thr == 0 || w.x < s_thr[0];
-    o.cat = leaf ? -1 : categorical(s_thr, w.x, 1, p.ncat_thr) - 1;
+    // the first two thresholds come from the parameter bank (no shared-memory load): they
+    // decide the leaf and the most probable term
+    leaf = p.ncat_thr == 0 || w.x < p.thr[0];
+    o.cat = leaf ? -1 : ((p.ncat_thr <= 1 || w.x < p.thr[1]) ? 0 : categorical(s_thr, w.x, 2, p.ncat_thr) - 1);
     S = uniform01<Real>(w.y);
     seg = leaf ? tau : tau * S;
     o.tau_c = tau * (Real(1) - S);
@@ -456,7 +458,7 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     leaf = (S >= tau) || (p.nterms == 0);
     seg = leaf ? tau : S;
     o.tau_c = tau - S;
-    o.cat = leaf ? -1 : categorical(s_thr, w.y, 0, p.ncat_thr);
+    o.cat = leaf ? -1 : ((p.ncat_thr == 0 || w.y < p.thr[0]) ? 0 : categorical(s_thr, w.y, 1, p.ncat_thr));
   }
   if constexpr ((FEAT & kFeatEuler) != 0) {
 #pragma unroll
