@@ -40,22 +40,24 @@ SM_COUNT_GB300 = 152
 ISSUE_PER_SM_PER_CLK = 4 * 32   # 4 schedulers x 1 warp-instruction x 32 threads
 
 
-def _walk_traffic():
-    """DRAM bytes per full-size walk launch from the committed ncu summary, or None when the
-    walk kernel's sources changed since that capture."""
+def _walk_profile():
+    """(DRAM bytes per full-size walk launch, issue-slot utilisation) from the committed ncu
+    summary, or (None, None) when the walk kernel's sources changed since that capture."""
     import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", "walk_kernel_sin2d.md")).read()
         want = re.search(r"source_sha256_16: ([0-9a-f]+)", text).group(1)
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+        m = re.search(r"issue_active_pct: ([0-9.]+)", text)
+        issue = float(m.group(1)) / 100.0 if m else None
         h = hashlib.sha256()
         for f in ("grt_device.cuh", "grt_walk.cuh"):
             with open(os.path.join(ROOT, "paper_2402_06491_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
-        return traffic if h.hexdigest()[:16] == want else None
+        return (traffic, issue) if h.hexdigest()[:16] == want else (None, None)
     except Exception:
-        return None
+        return None, None
 
 
 def _peaks():
@@ -598,6 +600,7 @@ def gpu_arm(args) -> int:
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT_GB300 * ISSUE_PER_SM_PER_CLK * sm_max * 1e6 / 1e12
+    walk_prof = _walk_profile()
     line = {
         "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -614,7 +617,11 @@ def gpu_arm(args) -> int:
         },
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-            "traffic": _walk_traffic() if not args.trees else None,
+            "traffic": walk_prof[0] if not args.trees else None,
+            "issue_active_ncu": walk_prof[1],
+            "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case; "
+                          "profiles/walk_kernel_sin2d.md): the hardware's SM issue-slot utilisation, "
+                          "beside the stricter algorithmic fraction `frac`",
             "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md); "
                             "algorithmic bytes are the 5 B/tree records = 256 MB written",
             "kernel": "walk_kernel<float,2,B> (persistent tree walk)",
