@@ -230,6 +230,23 @@ def test_edge_budgets_and_orders(grt):
         assert g["u"][0] == 0.0 and np.all(g["coef"][0] == 0.0)
 
 
+def test_zero_time_points(grt):
+    # t = 0: under Strategy A every root is a leaf (S >= 0 = tau) with weight g, so u = g exactly on
+    # both sides; under Strategy B the coin still runs (leaf weight g/q, split weight 0): parity only
+    wl = workloads.workload_kpp_1d()
+    x = wl["x"][:6]
+    t = np.zeros(6)
+    nt = np.full(6, 700, np.uint64)
+    g, o = _solve_both(grt, wl["problem"], x, t, nt, 8, 4, 4, 5)
+    g0 = np.array([oracle.u0(wl["problem"], xi) for xi in x])
+    assert np.allclose(o["u"], g0, rtol=1e-13, atol=0) and np.allclose(g["u"], g0, rtol=1e-13, atol=0)
+    assert np.all(g["coef"][:, 1:] == 0.0)
+    pb = workloads.problem_sin_2d()
+    xs = np.array([[0.2, -0.4], [1.5, 0.3], [-2.0, 2.0]])
+    g, o = _solve_both(grt, pb, xs, np.zeros(3), np.full(3, 5000, np.uint64), 10, 5, 5, 9)
+    _assert_fp32_parity(g, o, np.full(3, 5000, np.uint64), L=5, M=5)
+
+
 def test_empty_call(grt):
     ctx = grt.grt_create(workloads.problem_sin_2d(), 0)
     r = grt.grt_solve(ctx, np.zeros((0, 2)), np.zeros(0), np.zeros(0, np.uint64), 10, 5, 5, 0)
