@@ -153,3 +153,21 @@ def test_branching_thresholds_realise_the_law(oracle_mod):
     P = np.diff(np.concatenate([[0.0], thr]))
     assert np.allclose(tb["term_factor"] * P[1:], tb["coef"], rtol=1e-15, atol=0)
     assert abs(tb["leaf_factor"] * P[0] - 1.0) < 1e-15
+
+
+def test_cost_versus_final_time(oracle_mod):
+    """Sec. 2.4 / Fig. 6: Strategy B's work does not grow with t the way Strategy A's does.  Here
+    segments are exact, so under Strategy B a tree's topology (coin and term draws) does not
+    depend on t at all -- the same streams give the same trees and node counts for every t --
+    while under Strategy A the expected number of splits grows with t (Yule: e^{lambda t} - 1
+    for binary trees before pruning)."""
+    import numpy as np
+
+    pb_b = dict(dim=1, D=0.5, f_coef=[0.0, 0.0, 1.0], u0=("const", (0.5,)), strategy="B", q=2.0 / 3.0)
+    ref = oracle_mod.trees(pb_b, [0.0], 0.1, 0, 0, 4000, 12, 3)
+    for t in (0.5, 1.0, 4.0):
+        r = oracle_mod.trees(pb_b, [0.0], t, 0, 0, 4000, 12, 3)
+        assert np.array_equal(r["hash"], ref["hash"]) and np.array_equal(r["nodes"], ref["nodes"])
+    pb_a = dict(pb_b, strategy="A", lam=1.0, c_pot=0.0)
+    means = [oracle_mod.trees(pb_a, [0.0], t, 0, 0, 4000, 16, 3)["nodes"].mean() for t in (0.25, 0.5, 1.0)]
+    assert means[0] < means[1] < means[2]
