@@ -224,7 +224,10 @@ def reference_arm(args) -> int:
         return 0
     wl = workloads.WORKLOADS[WORKLOAD]()
     nthreads = os.cpu_count() or 1
-    per_step_s = float(os.environ.get("GRT_REFERENCE_STEP_S", "2.0"))
+    # a bounded sample per step, sized so that the whole run (warm-up + timed steps) takes about two
+    # minutes of host time whatever --steps is (at least one point per host thread per step)
+    budget_s = float(os.environ.get("GRT_REFERENCE_BUDGET_S", "120"))
+    per_step_s = float(os.environ.get("GRT_REFERENCE_STEP_S", str(min(2.0, budget_s / max(args.steps + args.warmup, 1)))))
     npts = oracle_sample(wl, per_step_s, nthreads)
     trees = float(np.sum(wl["ntrees"][:npts]))
     for _ in range(args.warmup):
