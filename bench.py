@@ -305,6 +305,32 @@ PDD_GRID = dict(dim=3, lo=[0.0] * 3, hi=[4.0] * 3, sub=[4] * 3, cells=[16] * 3, 
                 nsteps=100)
 
 
+def pdd_flops(g: dict) -> float:
+    """Algorithmic FP64 flops of grt_pdd_solve (FMA = 2): per subdomain step, 2 d sine-transform passes of
+    m_a flops-pairs per unknown plus the right-hand side (~40 flops per unknown: stencil, reaction, ring
+    terms); the spline's three contractions per plane family."""
+    d = g["dim"]
+    m = [c - 1 for c in g["cells"][:d]]
+    mloc = int(np.prod(m))
+    nsub = int(np.prod(g["sub"][:d]))
+    per_step = sum(2 * 2 * mloc * ma for ma in m) + 40 * mloc
+    cn = float(nsub) * g["nsteps"] * per_step
+    N = [g["sub"][a] * g["cells"][a] + 1 for a in range(d)]
+    spl = 0.0
+    tn = g["t_nodes"] + 1
+    for a in range(d):
+        np_ = g["sub"][a] + 1
+        oth = [b for b in range(d) if b != a]
+        pn = int(np.prod([g["nodes"][b] for b in oth])) if oth else 1
+        spl += 2.0 * np_ * g["nsteps"] * pn * tn
+        if len(oth) >= 1:
+            nc = g["nodes"][oth[1]] if len(oth) > 1 else 1
+            spl += 2.0 * np_ * g["nsteps"] * N[oth[0]] * nc * g["nodes"][oth[0]]
+        if len(oth) == 2:
+            spl += 2.0 * np_ * g["nsteps"] * N[oth[0]] * N[oth[1]] * g["nodes"][oth[1]]
+    return cn + spl
+
+
 def pdd_bench(grt, dev_index: int, steps: int) -> dict:
     """The 3-D interface problem end to end on the GPU: point solves at every plane's nodal points (the
     outer faces included) and time levels, then grt_pdd_solve (spline + 64 independent subdomain solves)."""
@@ -341,7 +367,16 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
     plan.close()
     ctx.close()
     nsub = int(np.prod(g["sub"]))
+    flops = pdd_flops(g)
+    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (not a tensor path); one block per subdomain uses nsub SMs
+    sms = 152
     return {"points": n, "trees": 100_000 * n, "grid_nodes": int(np.prod(N)), "subdomains": nsub,
+            "pdd_flops": flops, "pdd_fp64_tflops": flops / (pd / 1e3) / 1e12,
+            "pdd_roofline": {"bound": "fp64", "achieved": flops / (pd / 1e3) / 1e12, "peak": fp64_peak,
+                             "unit": "TFLOP/s", "frac": flops / (pd / 1e3) / 1e12 / fp64_peak,
+                             "frac_of_used_sms": flops / (pd / 1e3) / 1e12 / (fp64_peak * min(nsub, sms) / sms),
+                             "peak_basis": "nominal GB300 FP64 rate (no measured FP64 peak on this pool); "
+                                           "one thread block per subdomain runs on min(subdomains, 152) SMs"},
             "subdomain_unknowns": int(np.prod([c - 1 for c in g["cells"]])), "cn_steps": g["nsteps"],
             "point_solve_ms": mc, "pdd_stage_ms": pd, "total_ms": mc + pd, "steps": steps,
             "finite_output": finite,
