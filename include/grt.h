@@ -207,7 +207,7 @@ int grt_plan_launches(const grt_plan *plan);
 int grt_plan_set_config(grt_plan *plan, const int32_t *cfg);
 int grt_plan_get_config(const grt_plan *plan, int32_t *cfg);
 
-/* Autotuner (batching of uneven budgets): runs the plan on the
+/* Autotuner (batching of uneven budgets into one launch): runs the plan on the
  * given device buffers once per candidate shape (a warm run plus two timed runs,
  * CUDA events on `stream`), keeps the fastest walk, and returns it in cfg_out
  * [4] (may be NULL).  Leaves the outputs of a full solve in the buffers. */

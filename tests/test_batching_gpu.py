@@ -1,4 +1,4 @@
-"""Batching of uneven budgets (SURVEY NEXT-2): launch shapes, the autotuner and CUDA graphs.
+"""Batching of uneven budgets: launch shapes, the autotuner and CUDA graphs.
 
 The walk's launch shape (warps per block, stack levels in shared memory, blocks
 per SM, queue chunk size) must never change a result: the same trees are
