@@ -375,7 +375,7 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
             "pdd_roofline": {"bound": "fp64", "achieved": flops / (pd / 1e3) / 1e12, "peak": fp64_peak,
                              "unit": "TFLOP/s", "frac": flops / (pd / 1e3) / 1e12 / fp64_peak,
                              "frac_of_used_sms": flops / (pd / 1e3) / 1e12 / (fp64_peak * min(nsub, sms) / sms),
-                             "peak_basis": "nominal GB300 FP64 rate (no measured FP64 peak on this pool); "
+                             "peak_basis": "nominal GB300 FP64 rate (no measured FP64 peak is available); "
                                            "one thread block per subdomain runs on min(subdomains, 152) SMs"},
             "subdomain_unknowns": int(np.prod([c - 1 for c in g["cells"]])), "cn_steps": g["nsteps"],
             "point_solve_ms": mc, "pdd_stage_ms": pd, "total_ms": mc + pd, "steps": steps,

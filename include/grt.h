@@ -55,7 +55,7 @@ extern "C" {
 #define GRT_ENOMEM (-2)   /* device or pinned host memory could not be had   */
 #define GRT_EDEVICE (-3)  /* a CUDA call failed (no device, launch error...) */
 #define GRT_ETIMEOUT (-4) /* a bounded device wait ran out                   */
-#define GRT_ENOTSUP (-5)  /* valid request this build does not support       */
+#define GRT_ENOTSUP (-5)  /* valid request the library does not support      */
 #define GRT_EAGAIN 1      /* (grt_poll) the request has not finished yet      */
 
 /* Strategy (Sec. 2.1 / Sec. 2.2). */

@@ -4,7 +4,7 @@
  * arbitrary semilinear parabolic partial differential equations based on
  * generalized random trees" (arXiv 2402.06491).
  *
- * TEST INFRASTRUCTURE.  This file is the checker that the CUDA path is
+ * TEST INFRASTRUCTURE.  This file is the reference the CUDA path is
  * compared against.  Only the test suite, the smoke check and the benchmark's
  * CPU-baseline / reference arm load it.  The product library never links,
  * includes or calls it, and it shares no code, header, table or constant

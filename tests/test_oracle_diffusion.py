@@ -93,7 +93,7 @@ def test_a1_one_split_closed_form(oracle_mod, strategy, D, q, lam, c):
 
 
 def test_first_order_checker_against_brute_quadrature():
-    # the checker's Gaussian algebra against a direct 2-D quadrature of the same integral
+    # the helper's Gaussian algebra against a direct 2-D quadrature of the same integral
     from scipy import integrate
     D, A, s, b, t, x = 0.8, 1.1, 0.7, 1.0, 0.5, 0.3
 

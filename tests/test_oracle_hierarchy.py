@@ -88,7 +88,7 @@ def test_a_hierarchy_rk4(oracle_mod, f_coef, lam, c, c0, t):
 
 
 def test_ode_taylor_helper_against_closed_forms():
-    # the checker itself: phi' = phi^2 -> c0/(1 - c0 s); phi' = phi - phi^3 -> c0 e^s / sqrt(1 + c0^2 (e^{2s} - 1))
+    # the helper itself: phi' = phi^2 -> c0/(1 - c0 s); phi' = phi - phi^3 -> c0 e^s / sqrt(1 + c0^2 (e^{2s} - 1))
     phi = ode_taylor([0.0, 0.0, 1.0], 0.8, 8)
     assert np.allclose(phi, [0.8 ** (n + 1) for n in range(8)], rtol=1e-14)
     phi = ode_taylor([0.0, 1.0, 0.0, -1.0], 0.5, 12)
