@@ -355,3 +355,34 @@ def test_invalid_coefficient_profiles_rejected(grt):
     for pb in bad:
         with pytest.raises(grt.GrtError):
             grt.grt_create(pb, 0)
+
+
+@pytest.mark.parametrize("name,ctol", [("uneven_2d", 3e-5), ("pdd_3d", 1.5e-4), ("var_coef_2d", 3e-5),
+                                       ("drift_2d", 3e-5)])
+def test_full_size_workloads_sampled_points(grt, name, ctol):
+    """Every other benchmark workload at its full size, through the device-resident plan with the
+    autotuned launch shape the benchmark times; sampled points (spread over the index range and
+    the largest budget) recomputed one by one by the oracle (same global index)."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.WORKLOADS[name]()
+    n, K = wl["x"].shape[0], wl["K"]
+    dev = torch.device("cuda:0")
+    x, t = torch.from_numpy(wl["x"]).to(dev), torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = grt.grt_create(wl["problem"], 0)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, wl["L"], wl["M"])
+    grt.grt_plan_autotune(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    torch.cuda.synchronize()
+    g = dict(u=u.cpu().numpy(), coef=coef.cpu().numpy(), status=st.cpu().numpy())
+    plan.close()
+    ctx.close()
+    assert np.all(np.isfinite(g["u"]))
+    idx = sorted({0, n // 3, n // 2, (2 * n) // 3, n - 1, int(np.argmax(wl["ntrees"]))})
+    for i in idx:
+        o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], K, wl["L"],
+                         wl["M"], wl["seed"], point_base=i)
+        gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
+        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], ctol=ctol, L=wl["L"], M=wl["M"])
