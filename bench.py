@@ -199,23 +199,38 @@ def run_oracle(wl: dict, npts: int, nthreads: int):
     return time.perf_counter() - t0, r
 
 
-def cpu_baseline(wl: dict, target_s: float) -> dict:
+def cpu_baseline(wl: dict, target_s: float, gpu=None) -> dict:
     """The oracle, as it stands, on all host cores over the leading points of the workload.
 
-    Whole passes over the chosen points are repeated until about target_s of wall time.
+    Whole passes over the chosen points are repeated until about target_s of wall time.  When the
+    GPU's results for the same points (same streams) are given as gpu = (u, coef), the error of
+    each sampled result against the FP64 oracle is stated beside the timing.
     """
     nthreads = os.cpu_count() or 1
     npts = oracle_sample(wl, target_s, nthreads)
     trees = float(np.sum(wl["ntrees"][:npts]))
-    total, reps = 0.0, 0
+    total, reps, r = 0.0, 0, None
     while reps == 0 or (total < 0.5 * target_s and reps < 20):
-        dt, _ = run_oracle(wl, npts, nthreads)
+        dt, r = run_oracle(wl, npts, nthreads)
         total += dt
         reps += 1
     n = wl["x"].shape[0]
-    return {"value": trees * reps / total, "unit": "trees/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each) x {reps} pass(es), "
-                      f"{total:.1f} s wall on {nthreads} threads"}
+    out = {"value": trees * reps / total, "unit": "trees/s", "cores": nthreads, "kind": "oracle",
+           "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each) x {reps} pass(es), "
+                     f"{total:.1f} s wall on {nthreads} threads"}
+    if gpu is not None:
+        gu, gc = gpu
+        du = np.abs(gu[:npts] - r["u"])
+        scale = np.maximum(np.abs(r["u"]), np.abs(r["coef"]).sum(axis=1))  # the 1e-5 bar's scale
+        rel = du / np.maximum(scale, 1e-300)
+        out["error_vs_oracle"] = {
+            "points": npts, "bar": "|u_gpu - u_oracle| <= 1e-5 max(|u|, sum_n |a_n|)",
+            "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+            "within_bar": int((rel <= 1e-5).sum()),
+            "per_result_rel": [float(v) for v in rel],
+            "max_abs_coef": float(np.abs(gc[:npts] - r["coef"]).max()),
+        }
+    return out
 
 
 def reference_arm(args) -> int:
@@ -710,7 +725,8 @@ def gpu_arm(args) -> int:
         line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,
                                         float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")))
+        line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")),
+                                            gpu=(u_host, coef.cpu().numpy()) if point_base == 0 else None)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
