@@ -6,11 +6,14 @@
 //   * spline: a weights kernel (one thread per nodal column: the not-a-knot
 //     system of a unit data vector by elimination, then the cubic at every
 //     target) and an axis-contraction kernel applied once per axis, FP64;
-//   * local solver: one thread block per subdomain runs every time step with
-//     its four vectors in shared memory (global memory beyond 200 KB) and an
-//     exact fast-diagonalisation solve per step (DST-I along each axis as small
-//     dense FP64 contractions); the subdomains share nothing, which is the
-//     decoupling the method is built on (Sec. 3, "Local solver").
+//   * local solver: a cluster of two thread blocks per subdomain (each owning
+//     half of the rows, the peer's half read through distributed shared
+//     memory) -- or one block when a half does not fit in shared memory --
+//     runs every time step with an exact fast-diagonalisation solve per step
+//     (DST-I along each axis as small dense FP64 contractions); the subdomains
+//     share nothing, which is the decoupling the method is built on (Sec. 3,
+//     "Local solver").
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -317,6 +320,184 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
     for (int a = 0; a < DIM; ++a) off = off * q.N[a] + gi[a];
     q.u_out[off] = u[l];
   }
+}
+
+// The same steps with each subdomain split between the two blocks of a
+// cluster: block rank r owns the rows [r0, r1) of axis 0 (rank 0 the first
+// ceil(m0/2)), keeps its four vectors in its own shared memory and reads the
+// peer's rows through distributed shared memory for the axis-0 stencil and
+// the axis-0 sine transform.  Twice the SMs work on the same subdomains.
+// Order of a step: cluster barrier (the peer's u is final); right-hand side;
+// transforms along the in-row axes (local); cluster barrier; axis-0 transform
+// with the eigenvalue division; cluster barrier; axis-0 inverse transform;
+// cluster barrier (every peer read of this step is done); inverse in-row
+// transforms (local).
+template <int DIM, int NT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) cn_pair_kernel(const WalkParams p, const PddDev q) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double smem_vec[];
+  const unsigned crank = cl.block_rank();
+  const int sid = blockIdx.x >> 1;
+  int s[3] = {0, 0, 0};
+  {
+    int r = sid;
+#pragma unroll
+    for (int a = DIM - 1; a >= 0; --a) {
+      s[a] = r % q.sub[a];
+      r /= q.sub[a];
+    }
+  }
+  const int m0 = q.m[0];
+  const int h0 = (m0 + 1) >> 1;
+  const int r0 = crank ? h0 : 0, r1 = crank ? m0 : h0;
+  const int plane = q.mloc / m0;   // unknowns of one axis-0 row
+  const int nloc = (r1 - r0) * plane;
+  const int cap = h0 * plane;      // vector capacity: the larger half
+  double *mine = smem_vec;
+  double *peer = cl.map_shared_rank(smem_vec, (int)(crank ^ 1u));
+  // roles -> vector slots (both blocks rotate identically)
+  int ru = 0, rup = 1, ra = 2, rb = 3;
+  // in-row strides (axis 1, 2 within a row of the local storage)
+  int stride[3] = {plane, 1, 1};
+#pragma unroll
+  for (int a = DIM - 2; a >= 1; --a) stride[a] = stride[a + 1] * q.m[a + 1];
+  // value of role `role` at row g0 (global within the subdomain), in-row offset w
+  auto at = [&](int role, int g0, int w) -> double {
+    return g0 >= r0 && g0 < r1 ? mine[role * cap + (g0 - r0) * plane + w]
+                               : peer[role * cap + (g0 - (crank ? 0 : h0)) * plane + w];
+  };
+  auto node = [&](int l, int (&i)[3], int (&gi)[3], double (&xc)[3]) {
+    i[0] = r0 + l / plane;
+    int w = l % plane;
+#pragma unroll
+    for (int a = DIM - 1; a >= 1; --a) {
+      i[a] = w % q.m[a];
+      w /= q.m[a];
+    }
+    xc[0] = xc[1] = xc[2] = 0.0;
+    gi[0] = gi[1] = gi[2] = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      gi[a] = s[a] * q.cells[a] + 1 + i[a];
+      xc[a] = q.lo[a] + (double)gi[a] * q.h[a];
+    }
+  };
+  // in-row transform along axis ax >= 1 (local)
+  auto row_axis = [&](int ax, int rs, int rd) {
+    const int m = q.m[ax], st = stride[ax];
+    const double *__restrict__ S = q.S[ax];
+    const double *src = mine + rs * cap;
+    double *dst = mine + rd * cap;
+    for (int l = threadIdx.x; l < nloc; l += NT) {
+      int i[3], gi[3];
+      double xc[3];
+      node(l, i, gi, xc);
+      const double *col = src + (l - i[ax] * st);
+      const double *row = S + i[ax] * m;
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc = fma(__ldg(row + j), col[j * st], acc);
+      dst[l] = acc;
+    }
+  };
+  // axis-0 transform (reads both blocks' rows); with `scale` divides by 1 - alpha sum mu
+  auto axis0 = [&](int rs, int rd, bool scale) {
+    const double *__restrict__ S = q.S[0];
+    for (int l = threadIdx.x; l < nloc; l += NT) {
+      const int g0 = r0 + l / plane, w = l % plane;
+      const double *row = S + g0 * m0;
+      double acc = 0.0;
+      for (int j = 0; j < m0; ++j) acc = fma(__ldg(row + j), at(rs, j, w), acc);
+      if (scale) {
+        int i[3], gi[3];
+        double xc[3];
+        node(l, i, gi, xc);
+        double lam = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) lam += q.mu[a][i[a]];
+        acc = acc / (1.0 - q.alpha * lam);
+      }
+      mine[rd * cap + l] = acc;
+    }
+  };
+
+  for (int l = threadIdx.x; l < nloc; l += NT) {
+    int i[3], gi[3];
+    double xc[3];
+    node(l, i, gi, xc);
+    const double v = u0_at<DIM>(p, xc);
+    mine[ru * cap + l] = v;
+    mine[rup * cap + l] = v;
+  }
+  for (int n = 0; n < q.nsteps; ++n) {
+    cl.sync();  // the peer's u is final
+    const double th = ((double)n + 0.5) * q.dt;
+    for (int l = threadIdx.x; l < nloc; l += NT) {
+      int i[3], gi[3];
+      double xc[3];
+      node(l, i, gi, xc);
+      const int w = l % plane;
+      const double c = mine[ru * cap + l];
+      double lap = 0.0, ring1 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double left, right;
+        if (a == 0) {
+          left = i[0] > 0 ? at(ru, i[0] - 1, w) : ring_value<DIM>(p, q, s, gi, 0, 0, n);
+          right = i[0] < m0 - 1 ? at(ru, i[0] + 1, w) : ring_value<DIM>(p, q, s, gi, 0, 1, n);
+        } else {
+          left = i[a] > 0 ? mine[ru * cap + l - stride[a]] : ring_value<DIM>(p, q, s, gi, a, 0, n);
+          right = i[a] < q.m[a] - 1 ? mine[ru * cap + l + stride[a]] : ring_value<DIM>(p, q, s, gi, a, 1, n);
+        }
+        lap += (left + right - 2.0 * c) * q.inv_h2[a];
+        double rn = 0.0;
+        if (i[a] == 0) rn += ring_value<DIM>(p, q, s, gi, a, 0, n + 1);
+        if (i[a] == q.m[a] - 1) rn += ring_value<DIM>(p, q, s, gi, a, 1, n + 1);
+        ring1 += rn * q.inv_h2[a];
+      }
+      const double ustar = n == 0 ? c : 1.5 * c - 0.5 * mine[rup * cap + l];
+      mine[ra * cap + l] = c + q.alpha * lap + q.alpha * ring1 + q.dt * f_at<DIM>(p, q, xc, th, ustar);
+    }
+    __syncthreads();
+    int x = ra, y = rb;  // data in x
+#pragma unroll
+    for (int a = DIM - 1; a >= 1; --a) {
+      row_axis(a, x, y);
+      __syncthreads();
+      const int t = x;
+      x = y;
+      y = t;
+    }
+    cl.sync();          // the peer's rows are transformed along its in-row axes
+    axis0(x, y, true);  // into the sine basis along axis 0, divided by the eigenvalues
+    cl.sync();
+    axis0(y, x, false);  // back along axis 0
+    cl.sync();           // every read of the peer's rows in this step is done
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+      row_axis(a, x, y);
+      __syncthreads();
+      const int t = x;
+      x = y;
+      y = t;
+    }
+    // rotate: u^{n-1} <- u^n, u^n <- the solution; the freed slots are the next scratch
+    const int old_up = rup;
+    rup = ru;
+    ru = x;
+    ra = old_up;
+    rb = y;
+  }
+  for (int l = threadIdx.x; l < nloc; l += NT) {
+    int i[3], gi[3];
+    double xc[3];
+    node(l, i, gi, xc);
+    long long off = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) off = off * q.N[a] + gi[a];
+    q.u_out[off] = mine[ru * cap + l];
+  }
+  cl.sync();  // the peer may still read this block's shared memory until here
 }
 
 // Plane nodes of the output: the spline at T, the lowest axis's plane on edges.
@@ -698,26 +879,27 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   long long ntot = 1;
   for (int a = 0; a < d; ++a) ntot *= q.N[a];
   const size_t smem = q.use_smem ? vec_bytes : 0;
+  // a pair of blocks (a cluster) per subdomain when each half fits in shared memory
+  const int h0 = (q.m[0] + 1) / 2;
+  const size_t pair_bytes = 4 * (size_t)h0 * (q.mloc / q.m[0]) * sizeof(double);
+  const bool pair = q.m[0] >= 2 && pair_bytes <= kPddSmemBytes;
+#define GRT_CN_LAUNCH(D)                                                                                          \
+  if (pair) {                                                                                                    \
+    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_pair_kernel<D, kPddThreads>,                                        \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));          \
+    grt::cn_pair_kernel<D, kPddThreads><<<(unsigned)(2 * nsub), kPddThreads, pair_bytes, s>>>(c->base, q);       \
+  } else {                                                                                                       \
+    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<D, kPddThreads>,                                   \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));          \
+    grt::cn_subdomain_kernel<D, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);              \
+  }                                                                                                              \
+  grt::pdd_planes_kernel<D><<<grid_for(ntot), 256, 0, s>>>(q);
   switch (d) {
-  case 1:
-    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<1, kPddThreads>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
-    grt::cn_subdomain_kernel<1, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
-    grt::pdd_planes_kernel<1><<<grid_for(ntot), 256, 0, s>>>(q);
-    break;
-  case 2:
-    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<2, kPddThreads>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
-    grt::cn_subdomain_kernel<2, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
-    grt::pdd_planes_kernel<2><<<grid_for(ntot), 256, 0, s>>>(q);
-    break;
-  default:
-    GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<3, kPddThreads>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));
-    grt::cn_subdomain_kernel<3, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);
-    grt::pdd_planes_kernel<3><<<grid_for(ntot), 256, 0, s>>>(q);
-    break;
+  case 1: GRT_CN_LAUNCH(1) break;
+  case 2: GRT_CN_LAUNCH(2) break;
+  default: GRT_CN_LAUNCH(3) break;
   }
+#undef GRT_CN_LAUNCH
   GRT_CUDA(c, cudaGetLastError());
   return GRT_OK;
 }

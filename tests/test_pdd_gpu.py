@@ -65,7 +65,8 @@ def _pdd_problem(dim):
 
 @pytest.mark.parametrize("dim,sub,cells,nodes", [(1, [4], [9], [4]), (2, [3, 2], [7, 5], [7, 6]),
                                                  (3, [2, 3, 2], [6, 5, 7], [6, 7, 5]),
-                                                 (3, [1, 1, 2], [20, 20, 20], [5, 5, 5])])  # vectors in global memory
+                                                 (3, [1, 1, 2], [20, 20, 20], [5, 5, 5]),  # block pairs
+                                                 (3, [1, 1, 2], [30, 30, 30], [5, 5, 5])])  # global-memory vectors
 def test_pdd_solve_parity(grt, torch, dim, sub, cells, nodes):
     g = dict(dim=dim, lo=[0.0] * dim, hi=[float(s) for s in sub], sub=sub, cells=cells, nodes=nodes, t_nodes=4,
              T=0.6, nsteps=24)
