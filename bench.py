@@ -383,15 +383,21 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
     ctx.close()
     nsub = int(np.prod(g["sub"]))
     flops = pdd_flops(g)
-    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (not a tensor path); one block per subdomain uses nsub SMs
+    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (not a tensor path)
     sms = 152
+    # blocks per subdomain: a cluster pair when half of the subdomain's four vectors fits in 200 KB
+    m = [c - 1 for c in g["cells"]]
+    half = 4 * ((m[0] + 1) // 2) * int(np.prod(m[1:])) * 8
+    per_sub = 2 if m[0] >= 2 and half <= 200 * 1024 else 1
     return {"points": n, "trees": 100_000 * n, "grid_nodes": int(np.prod(N)), "subdomains": nsub,
             "pdd_flops": flops, "pdd_fp64_tflops": flops / (pd / 1e3) / 1e12,
             "pdd_roofline": {"bound": "fp64", "achieved": flops / (pd / 1e3) / 1e12, "peak": fp64_peak,
                              "unit": "TFLOP/s", "frac": flops / (pd / 1e3) / 1e12 / fp64_peak,
-                             "frac_of_used_sms": flops / (pd / 1e3) / 1e12 / (fp64_peak * min(nsub, sms) / sms),
+                             "frac_of_used_sms": flops / (pd / 1e3) / 1e12
+                             / (fp64_peak * min(per_sub * nsub, sms) / sms),
+                             "blocks_per_subdomain": per_sub,
                              "peak_basis": "nominal GB300 FP64 rate (no measured FP64 peak is available); "
-                                           "one thread block per subdomain runs on min(subdomains, 152) SMs"},
+                                           "the subdomain blocks run on min(blocks, 152) SMs"},
             "subdomain_unknowns": int(np.prod([c - 1 for c in g["cells"]])), "cn_steps": g["nsteps"],
             "point_solve_ms": mc, "pdd_stage_ms": pd, "total_ms": mc + pd, "steps": steps,
             "finite_output": finite,
