@@ -383,6 +383,16 @@ int grt_pdd_points(const grt_pdd_grid *g, int64_t capacity, double *x, double *t
  * context's, or a subdomain above GRT_PDD_MAX_LOCAL unknowns. */
 int grt_pdd_solve(grt_ctx *ctx, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, void *stream);
 
+/* The same for the subdomains [sub_begin, sub_end) of the row-major subdomain
+ * numbering (axis 0 slowest) only: the spline stages run in full, every plane
+ * node of d_u_out is written, and only these subdomains' interior nodes; the
+ * other interiors are left as they are.  The subdomains are independent (Sec.
+ * 3: the decoupled sub-problems), so disjoint ranges on different GPUs -- each
+ * with all nodal values -- together give grt_pdd_solve's result bit for bit.
+ * GRT_EINVAL unless 0 <= sub_begin <= sub_end <= prod_a sub[a]. */
+int grt_pdd_solve_range(grt_ctx *ctx, const grt_pdd_grid *g, int64_t sub_begin, int64_t sub_end,
+                        const double *d_u_nodes, double *d_u_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

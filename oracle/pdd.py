@@ -73,6 +73,8 @@ def u0_grid(pb: dict, X: list) -> np.ndarray:
     if kind == "gauss_axes":
         r = sum(p[2 + i] * (X[i] - p[5 + i]) ** 2 for i in range(d))
         return p[0] + p[1] * np.exp(-r)
+    if kind == "quadratic":
+        return p[0] + sum(p[1 + i] * X[i] + p[4 + i] * X[i] ** 2 for i in range(d))
     raise ValueError(kind)
 
 
@@ -352,9 +354,11 @@ def _ring_from_planes(g, P: dict, n: int, lo_idx: list, hi_idx: list) -> np.ndar
     return U
 
 
-def pdd_solve(pb: dict, g, u_nodes: np.ndarray, plane_data: dict | None = None) -> np.ndarray:
+def pdd_solve(pb: dict, g, u_nodes: np.ndarray, plane_data: dict | None = None,
+              subdomains: tuple | None = None) -> np.ndarray:
     """The PDD solution at t = T on the global FD grid: planes from the spline of u_nodes (or the given
-    per-level plane data), subdomain interiors from independent Crank-Nicolson solves."""
+    per-level plane data), subdomain interiors from independent Crank-Nicolson solves -- all of them, or
+    only those of the row-major range `subdomains` = (begin, end) (other interiors stay 0)."""
     d = g["dim"]
     N, coords = _axes(g)
     P = plane_data if plane_data is not None else plane_values(pb, g, u_nodes)
@@ -366,7 +370,9 @@ def pdd_solve(pb: dict, g, u_nodes: np.ndarray, plane_data: dict | None = None) 
             idx = [slice(None)] * d
             idx[a] = k * g["cells"][a]
             out[tuple(idx)] = P[(a, k)][g["nsteps"]]
-    for s in np.ndindex(*[g["sub"][a] for a in range(d)]):
+    for sid, s in enumerate(np.ndindex(*[g["sub"][a] for a in range(d)])):
+        if subdomains is not None and not subdomains[0] <= sid < subdomains[1]:
+            continue
         lo_idx = [s[a] * g["cells"][a] for a in range(d)]
         hi_idx = [(s[a] + 1) * g["cells"][a] for a in range(d)]
         sub_coords = [coords[a][lo_idx[a]: hi_idx[a] + 1] for a in range(d)]

@@ -114,6 +114,7 @@ def _load():
         "grt_spline_grid": ([_vp, i32, i32p, f64p, f64p, i32p, f64p, i64, _vp, _vp, _vp], i32),
         "grt_pdd_points": ([_P(grt_pdd_grid), i64, f64p, f64p, _P(ctypes.c_int64)], i32),
         "grt_pdd_solve": ([_vp, _P(grt_pdd_grid), _vp, _vp, _vp], i32),
+        "grt_pdd_solve_range": ([_vp, _P(grt_pdd_grid), i64, i64, _vp, _vp, _vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -551,15 +552,27 @@ def grt_pdd_points(grid: dict):
     return x, t
 
 
-def grt_pdd_solve(ctx: Context, grid: dict, u_nodes, u_out, stream=None) -> None:
+def grt_pdd_solve(ctx: Context, grid: dict, u_nodes, u_out, stream=None, subdomains=None) -> None:
     """Enqueue the PDD solution at T on the global grid into the device buffer u_out (N[0] x ... row-major).
-    u_nodes: device values at grt_pdd_points."""
+    u_nodes: device values at grt_pdd_points.  subdomains=(begin, end) solves only that range of the
+    row-major subdomain numbering (grt_pdd_solve_range)."""
     lib = _load()
     gs = pdd_grid_struct(grid)
     sh = None
     if stream is not None:
         sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    _check(lib.grt_pdd_solve(ctx.handle, ctypes.byref(gs), _devptr(u_nodes), _devptr(u_out), sh), ctx.handle)
+    if subdomains is None:
+        rc = lib.grt_pdd_solve(ctx.handle, ctypes.byref(gs), _devptr(u_nodes), _devptr(u_out), sh)
+    else:
+        rc = lib.grt_pdd_solve_range(ctx.handle, ctypes.byref(gs), int(subdomains[0]), int(subdomains[1]),
+                                     _devptr(u_nodes), _devptr(u_out), sh)
+    _check(rc, ctx.handle)
+
+
+def grt_pdd_solve_range(ctx: Context, grid: dict, sub_begin: int, sub_end: int, u_nodes, u_out,
+                        stream=None) -> None:
+    """grt_pdd_solve for the row-major subdomains [sub_begin, sub_end) only (all plane nodes written)."""
+    grt_pdd_solve(ctx, grid, u_nodes, u_out, stream=stream, subdomains=(sub_begin, sub_end))
 
 
 def grt_spline_grid(ctx: Context, n_nodes, lo, hi, targets, values, out, batch: int = 1, stream=None) -> None:
@@ -587,4 +600,4 @@ EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_pla
             "grt_plan_graph_launch",
             "grt_pade", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",
-            "grt_pdd_points", "grt_pdd_solve"]
+            "grt_pdd_points", "grt_pdd_solve", "grt_pdd_solve_range"]

@@ -116,6 +116,7 @@ struct PddDev {
   double *work;              // [nsub][4][mloc] when the vectors do not fit in shared memory
   int mloc;
   int use_smem;
+  int sub_first;             // first subdomain (row-major index) of this launch
   double *u_out;
 };
 
@@ -218,7 +219,7 @@ __device__ __forceinline__ void dst_axis(const PddDev &q, int ax, const int (&st
 template <int DIM, int NT>
 __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, const PddDev q) {
   extern __shared__ double smem_vec[];
-  const int sid = blockIdx.x;
+  const int sid = q.sub_first + (int)blockIdx.x;
   int s[3] = {0, 0, 0};
   {
     int r = sid;
@@ -338,7 +339,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) cn_pair_kernel(c
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double smem_vec[];
   const unsigned crank = cl.block_rank();
-  const int sid = blockIdx.x >> 1;
+  const int sid = q.sub_first + (int)(blockIdx.x >> 1);
   int s[3] = {0, 0, 0};
   {
     int r = sid;
@@ -718,10 +719,15 @@ int grt_spline_grid(grt_ctx *c, int ndim, const int32_t *n_nodes, const double *
   return GRT_OK;
 }
 
-int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, void *stream) {
+int grt_pdd_solve_range(grt_ctx *c, const grt_pdd_grid *g, int64_t sub_begin, int64_t sub_end,
+                        const double *d_u_nodes, double *d_u_out, void *stream) {
   if (!c) return GRT_EINVAL;
   int rc = check_grid(c, g);
   if (rc != GRT_OK) return rc;
+  long long nsub_all = 1;
+  for (int a = 0; a < g->dim; ++a) nsub_all *= g->sub[a];
+  if (sub_begin < 0 || sub_end > nsub_all || sub_begin > sub_end)
+    return c->set_error(GRT_EINVAL, "need 0 <= sub_begin <= sub_end <= number of subdomains");
   if (c->pb.sde_kind != GRT_SDE_HEAT)
     return c->set_error(GRT_ENOTSUP, "the PDD local solver discretises D Lap: paths must be GRT_SDE_HEAT");
   if (!d_u_nodes || !d_u_out) return c->set_error(GRT_EINVAL, "u_nodes and u_out must be non-NULL");
@@ -879,6 +885,8 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   long long ntot = 1;
   for (int a = 0; a < d; ++a) ntot *= q.N[a];
   const size_t smem = q.use_smem ? vec_bytes : 0;
+  q.sub_first = (int)sub_begin;
+  const long long nrun = sub_end - sub_begin;  // subdomains solved by this call
   // a pair of blocks (a cluster) per subdomain when each half fits in shared memory
   const int h0 = (q.m[0] + 1) / 2;
   const size_t pair_bytes = 4 * (size_t)h0 * (q.mloc / q.m[0]) * sizeof(double);
@@ -887,11 +895,13 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
   if (pair) {                                                                                                    \
     GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_pair_kernel<D, kPddThreads>,                                        \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));          \
-    grt::cn_pair_kernel<D, kPddThreads><<<(unsigned)(2 * nsub), kPddThreads, pair_bytes, s>>>(c->base, q);       \
+    if (nrun > 0)                                                                                                \
+      grt::cn_pair_kernel<D, kPddThreads><<<(unsigned)(2 * nrun), kPddThreads, pair_bytes, s>>>(c->base, q);     \
   } else {                                                                                                       \
     GRT_CUDA(c, cudaFuncSetAttribute(grt::cn_subdomain_kernel<D, kPddThreads>,                                   \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPddSmemBytes));          \
-    grt::cn_subdomain_kernel<D, kPddThreads><<<(unsigned)nsub, kPddThreads, smem, s>>>(c->base, q);              \
+    if (nrun > 0)                                                                                                \
+      grt::cn_subdomain_kernel<D, kPddThreads><<<(unsigned)nrun, kPddThreads, smem, s>>>(c->base, q);            \
   }                                                                                                              \
   grt::pdd_planes_kernel<D><<<grid_for(ntot), 256, 0, s>>>(q);
   switch (d) {
@@ -902,6 +912,15 @@ int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, do
 #undef GRT_CN_LAUNCH
   GRT_CUDA(c, cudaGetLastError());
   return GRT_OK;
+}
+
+int grt_pdd_solve(grt_ctx *c, const grt_pdd_grid *g, const double *d_u_nodes, double *d_u_out, void *stream) {
+  if (!c) return GRT_EINVAL;
+  int rc = check_grid(c, g);
+  if (rc != GRT_OK) return rc;
+  long long nsub_all = 1;
+  for (int a = 0; a < g->dim; ++a) nsub_all *= g->sub[a];
+  return grt_pdd_solve_range(c, g, 0, nsub_all, d_u_nodes, d_u_out, stream);
 }
 
 }  // extern "C"

@@ -172,3 +172,28 @@ def test_pdd_3d_end_to_end_against_the_global_solve(grt, torch):
     err = np.abs(G - U).max()
     assert err <= bound, (err, bound, e_if, e_int, lam)
     assert e_if < 0.05, e_if  # the interface values themselves: Monte Carlo sized at T = 1/4
+
+
+@pytest.mark.parametrize("cells", [[5, 6, 4], [30, 30, 30]])  # block pairs; one block with global vectors
+def test_pdd_subdomain_ranges_reproduce_the_full_solve(grt, torch, cells):
+    """Disjoint subdomain ranges (what different GPUs would solve) together give the full solve
+    bit for bit; each range call writes every plane node and only its own interiors."""
+    from paper_2402_06491_gb300.sharding import pdd_subdomain_range
+
+    sub = [2, 2, 2] if cells[0] < 30 else [1, 1, 2]
+    g = dict(dim=3, lo=[0.0] * 3, hi=[float(v) for v in sub], sub=sub, cells=cells, nodes=[5, 5, 5], t_nodes=4,
+             T=0.4, nsteps=12)
+    pb = _pdd_problem(3)
+    x, t = grt.grt_pdd_points(g)
+    u_nodes = torch.from_numpy(0.3 * np.sin(x.sum(axis=1)) + 0.1 * t + 0.2).cuda()
+    ctx = grt.grt_create(pb, 0)
+    N = [sub[a] * cells[a] + 1 for a in range(3)]
+    full = torch.empty(N, dtype=torch.float64, device="cuda")
+    grt.grt_pdd_solve(ctx, g, u_nodes, full)
+    parts = torch.zeros(N, dtype=torch.float64, device="cuda")
+    for rank in range(3):  # three "ranks" over the subdomains
+        grt.grt_pdd_solve_range(ctx, g, *pdd_subdomain_range(g, 3, rank), u_nodes, parts)
+    assert torch.equal(parts, full)
+    with pytest.raises(grt.GrtError):
+        grt.grt_pdd_solve_range(ctx, g, 0, int(np.prod(sub)) + 1, u_nodes, parts)
+    ctx.close()

@@ -64,3 +64,60 @@ def test_two_rank_gloo_shards_match_single_rank(tmp_path):
     wl = workloads.subsample(workloads.workload_sin_2d(), 10, ntrees=1500)
     full = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
     assert np.array_equal(got, full["u"])
+
+
+def _pdd_rank_main(rank, world, port, out_dir):
+    """Rank r solves its shard of the nodal points, all-gathers the nodal values (the method's one
+    exchange), then solves its own range of the decoupled subdomains; the CPU oracle stands in for
+    both GPU stages."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from oracle import pdd
+    from paper_2402_06491_gb300.sharding import pdd_subdomain_range
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    pb = dict(workloads.problem_pdd_3d(), D=0.3)
+    grid = dict(dim=2, lo=[0.0, 0.0], hi=[3.0, 2.0], sub=[3, 2], cells=[6, 6], nodes=[5, 5], t_nodes=3, T=0.3,
+                nsteps=6)
+    pb2 = dict(pb, dim=2, u0=("tanh_prod", (0.0, 1.0, 1.5, 1.0)))
+    x, t = pdd.points(grid)
+    n = x.shape[0]
+    a, b = shard_range(n, world, rank)
+    r = oracle.solve(pb2, x[a:b], t[a:b], np.full(b - a, 300, np.uint64), 6, 3, 3, 0, point_base=a, nthreads=1)
+    counts = [shard_range(n, world, k)[1] - shard_range(n, world, k)[0] for k in range(world)]
+    mine = torch.zeros(max(counts), dtype=torch.float64)
+    mine[: b - a] = torch.from_numpy(r["u"])
+    parts = [torch.zeros(max(counts), dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, mine)
+    u_nodes = np.concatenate([parts[k][: counts[k]].numpy() for k in range(world)])
+    s0, s1 = pdd_subdomain_range(grid, world, rank)
+    part = pdd.pdd_solve(pb2, grid, u_nodes, subdomains=(s0, s1))
+    np.save(os.path.join(out_dir, f"pdd_{rank}.npy"), part)
+    np.save(os.path.join(out_dir, f"nodes_{rank}.npy"), u_nodes)
+    dist.destroy_process_group()
+
+
+def test_pdd_subdomains_shard_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+
+    from oracle import pdd
+
+    world, port = 2, 29000 + (os.getpid() % 2000)
+    mp.start_processes(_pdd_rank_main, args=(world, port, str(tmp_path)), nprocs=world, start_method="spawn")
+    nodes = [np.load(os.path.join(tmp_path, f"nodes_{k}.npy")) for k in range(world)]
+    assert np.array_equal(nodes[0], nodes[1])
+    parts = [np.load(os.path.join(tmp_path, f"pdd_{k}.npy")) for k in range(world)]
+    pb2 = dict(workloads.problem_pdd_3d(), D=0.3, dim=2, u0=("tanh_prod", (0.0, 1.0, 1.5, 1.0)))
+    grid = dict(dim=2, lo=[0.0, 0.0], hi=[3.0, 2.0], sub=[3, 2], cells=[6, 6], nodes=[5, 5], t_nodes=3, T=0.3,
+                nsteps=6)
+    full = pdd.pdd_solve(pb2, grid, nodes[0])
+    # interiors are disjoint (zero elsewhere) and plane nodes identical: rank 0's planes + both interiors
+    planes = np.zeros(full.shape, bool)
+    planes[::6, :] = True
+    planes[:, ::6] = True
+    combined = np.where(planes, parts[0], parts[0] + parts[1])
+    assert np.array_equal(combined, full)
