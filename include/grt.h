@@ -85,9 +85,10 @@ extern "C" {
  *   dX_i = (beta_i - kappa_i X_i) dt + (s_i + r_i X_i) dW_i,
  * sde_param = {beta[3], kappa[3], s[3], r[3]}, D unused, by Euler-Maruyama
  * (the Euler scheme of Sec. 2.4) with sde_steps equal steps per segment;
- * step j of a node draws one Philox4x32-10 block at the node's counter with
- * the sub bit set under the key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1) 0x6C8E9CF5),
- * normals by Box-Muller on (w0, w1) and, for d = 3, (w2, w3). */
+ * the normals come from Philox4x32-10 blocks at the node's counter with the
+ * sub bit set, block b under the key (k0 ^ (b+1) 0x2545F491, k1 ^ (b+1)
+ * 0x6C8E9CF5), Box-Muller on its word pairs: for d <= 2 block b serves steps
+ * 2b ((w0, w1)) and 2b + 1 ((w2, w3)); for d = 3 block b serves step b. */
 #define GRT_SDE_HEAT 0
 #define GRT_SDE_AFFINE 1
 

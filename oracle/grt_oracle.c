@@ -353,10 +353,19 @@ static void or_hash_code(or_tree *T, uint64_t code)
  * segment of length s_seg (Eqs. SDE, green: the paths of a general operator L
  * = a_ij d_i d_j + b_i d_i with sigma^2 = a, simulated by the Euler scheme as
  * in Sec. 2.4).  A fixed number m = sde_steps of equal steps h = s_seg / m.
- * Step j draws from its own Philox key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1)
- * 0x6C8E9CF5) at the node's counter with the sub bit set; its normals are
- * Box-Muller on (w0, w1): n0 = r cos(2 pi U1), n1 = r sin(2 pi U1), and for
- * d = 3 n2 = sqrt(-2 ln U2) cos(2 pi U3). */
+ * Normals come from Philox blocks at the node's counter with the sub bit set,
+ * block b under the key (k0 ^ (b+1) 0x2545F491, k1 ^ (b+1) 0x6C8E9CF5), each
+ * Box-Muller pair (u, v) giving r cos(2 pi v), r sin(2 pi v), r = sqrt(-2 ln u):
+ *   d <= 2: block b serves steps 2b (pair (w0, w1)) and 2b + 1 (pair (w2, w3));
+ *   d = 3:  block b serves step b: (w0, w1) -> n0, n1 and (w2, w3) -> n2 (cos). */
+static void or_bm_pair(uint32_t wu, uint32_t wv, double *z0, double *z1)
+{
+    double r = sqrt(-2.0 * log(oracle_uniform(wu)));
+    double a = 2.0 * M_PI * oracle_uniform(wv);
+    *z0 = r * cos(a);
+    *z1 = r * sin(a);
+}
+
 static void or_euler_segment(const or_tree *T, const or_problem *pb, const double *x, double s_seg, uint64_t id,
                              double *y)
 {
@@ -366,18 +375,25 @@ static void or_euler_segment(const or_tree *T, const or_problem *pb, const doubl
     int m = pb->sde_steps;
     double h = s_seg / (double)m, sh = sqrt(h);
     for (int i = 0; i < d; ++i) y[i] = x[i];
+    uint32_t w[4] = { 0, 0, 0, 0 };
     for (int j = 0; j < m; ++j) {
-        uint32_t jj = (uint32_t)(j + 1);
-        uint32_t key[2] = { T->key[0] ^ (jj * 0x2545F491u), T->key[1] ^ (jj * 0x6C8E9CF5u) };
-        uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32), T->tree | 0x80000000u, T->point };
-        uint32_t w[4];
-        oracle_philox4x32_10(ctr, key, w);
-        double z[3];
-        double r0 = sqrt(-2.0 * log(oracle_uniform(w[0])));
-        double a0 = 2.0 * M_PI * oracle_uniform(w[1]);
-        z[0] = r0 * cos(a0);
-        z[1] = r0 * sin(a0);
-        z[2] = sqrt(-2.0 * log(oracle_uniform(w[2]))) * cos(2.0 * M_PI * oracle_uniform(w[3]));
+        int b = (d <= 2) ? j / 2 : j;
+        int first = (d <= 2) ? (j % 2 == 0) : 1;
+        if (first) {
+            uint32_t bb = (uint32_t)(b + 1);
+            uint32_t key[2] = { T->key[0] ^ (bb * 0x2545F491u), T->key[1] ^ (bb * 0x6C8E9CF5u) };
+            uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32), T->tree | 0x80000000u, T->point };
+            oracle_philox4x32_10(ctr, key, w);
+        }
+        double z[3], dummy;
+        if (d <= 2) {
+            if (j % 2 == 0) or_bm_pair(w[0], w[1], &z[0], &z[1]);
+            else or_bm_pair(w[2], w[3], &z[0], &z[1]);
+            z[2] = 0.0;
+        } else {
+            or_bm_pair(w[0], w[1], &z[0], &z[1]);
+            or_bm_pair(w[2], w[3], &z[2], &dummy);
+        }
         for (int i = 0; i < d; ++i) {
             double X = y[i];
             y[i] = X + (beta[i] - kappa[i] * X) * h + (sd[i] + rr[i] * X) * sh * z[i];

@@ -353,8 +353,22 @@ template <> __device__ __forceinline__ double sdeconst<double>(const WalkParams 
 // Euler-Maruyama over a segment of length seg for dX_i = (beta_i - kappa_i X_i) dt
 // + (s_i + r_i X_i) dW_i (the Euler scheme of Sec. 2.4 for the SDE of a general
 // operator), sde_steps equal steps.  The walk carries displacements y from the
-// root; X = x_p + y.  Step j: one Philox block at the node's counter with the
-// sub bit set, under the key (k0 ^ (j+1) 0x2545F491, k1 ^ (j+1) 0x6C8E9CF5).
+// root; X = x_p + y.  Normals come from Philox blocks at the node's counter with
+// the sub bit set, block b under the key (k0 ^ (b+1) 0x2545F491, k1 ^ (b+1)
+// 0x6C8E9CF5), Box-Muller on its word pairs: for d <= 2 block b serves steps 2b
+// ((w0, w1)) and 2b + 1 ((w2, w3)); for d = 3 block b serves step b ((w0, w1) for
+// n0, n1 and (w2, w3) for n2).
+template <typename Real, int DIM>
+__device__ __forceinline__ void euler_step(const WalkParams &p, const Real (&x0)[DIM], Real h, Real sh,
+                                           const Real (&z)[3], Real (&y)[DIM]) {
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    const Real X = x0[i] + y[i];
+    y[i] += (sdeconst<Real>(p, i) - sdeconst<Real>(p, 3 + i) * X) * h +
+            (sdeconst<Real>(p, 6 + i) + sdeconst<Real>(p, 9 + i) * X) * sh * z[i];
+  }
+}
+
 template <typename Real, int DIM>
 __device__ __forceinline__ void euler_segment(const WalkParams &p, const double *__restrict__ xp, Real seg,
                                               uint32_t id_lo, uint32_t id_hi, uint32_t tree, uint32_t point,
@@ -367,22 +381,33 @@ __device__ __forceinline__ void euler_segment(const WalkParams &p, const double 
 #pragma unroll
   for (int i = 0; i < DIM; ++i) x0[i] = (Real)xp[i];
   const uint32_t k0 = p.rk0[0], k1 = p.rk1[0];
-  for (int j = 0; j < m; ++j) {
-    const uint32_t jj = (uint32_t)(j + 1);
-    const uint4 w = philox4x32_10_key(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), k0 ^ (jj * 0x2545F491u),
-                                      k1 ^ (jj * 0x6C8E9CF5u));
+  const int nblocks = DIM <= 2 ? (m + 1) / 2 : m;
+  for (int b = 0; b < nblocks; ++b) {
+    const uint32_t bb = (uint32_t)(b + 1);
+    const uint4 w = philox4x32_10_key(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), k0 ^ (bb * 0x2545F491u),
+                                      k1 ^ (bb * 0x6C8E9CF5u));
     Real z[3];
-    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.x)));
-    Real sn, cs;
-    F::sincos2pi_w(w.y, &sn, &cs);
-    z[0] = r * cs;
-    z[1] = r * sn;
-    z[2] = DIM == 3 ? F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z))) * F::cos2pi_w(w.w) : Real(0);
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      const Real X = x0[i] + y[i];
-      y[i] += (sdeconst<Real>(p, i) - sdeconst<Real>(p, 3 + i) * X) * h +
-              (sdeconst<Real>(p, 6 + i) + sdeconst<Real>(p, 9 + i) * X) * sh * z[i];
+    {
+      const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.x)));
+      Real sn, cs;
+      F::sincos2pi_w(w.y, &sn, &cs);
+      z[0] = r * cs;
+      z[1] = r * sn;
+    }
+    if constexpr (DIM == 3) {
+      z[2] = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z))) * F::cos2pi_w(w.w);
+      euler_step<Real, DIM>(p, x0, h, sh, z, y);
+    } else {
+      z[2] = Real(0);
+      euler_step<Real, DIM>(p, x0, h, sh, z, y);
+      if (2 * b + 1 < m) {
+        const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z)));
+        Real sn, cs;
+        F::sincos2pi_w(w.w, &sn, &cs);
+        z[0] = r * cs;
+        z[1] = r * sn;
+        euler_step<Real, DIM>(p, x0, h, sh, z, y);
+      }
     }
   }
 }
