@@ -113,6 +113,7 @@ struct PddDev {
   uint32_t coef_pow_mask;    // powers k whose coefficient is b_k gamma(x, t)
   const double *S[3];        // per axis: the m x m orthonormal DST-I matrix
   const double *mu[3];       // per axis: eigenvalues of the 1-D Dirichlet second difference
+  const double *inv_eig;     // [mloc] 1 / (1 - alpha sum_a mu_a(i_a)), subdomain-local row-major index
   double *work;              // [nsub][4][mloc] when the vectors do not fit in shared memory
   int mloc;
   int use_smem;
@@ -133,6 +134,20 @@ __global__ void dst_tables_kernel(int m, double h, double *__restrict__ S, doubl
   if (j == 0) {
     const double sv = sinpi((double)(i + 1) / (2.0 * (double)(m + 1)));
     mu[i] = -4.0 / (h * h) * sv * sv;
+  }
+}
+
+// inv[l] = 1 / (1 - alpha sum_a mu_a(i_a)) for the subdomain-local row-major index l:
+// the eigenvalues of I - alpha Lap_h, inverted once per solve instead of per step
+__global__ void inv_eig_kernel(int dim, int m0, int m1, int m2, double alpha, const double *__restrict__ mu0,
+                               const double *__restrict__ mu1, const double *__restrict__ mu2, double *__restrict__ inv) {
+  const int n = m0 * m1 * m2;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+    const int i2 = l % m2, i1 = (l / m2) % m1, i0 = l / (m1 * m2);
+    double lam = mu0[i0];
+    if (dim > 1) lam += mu1[i1];
+    if (dim > 2) lam += mu2[i2];
+    inv[l] = 1.0 / (1.0 - alpha * lam);
   }
 }
 
@@ -288,14 +303,8 @@ __global__ void __launch_bounds__(NT) cn_subdomain_kernel(const WalkParams p, co
       src = dst;
       dst = t;
     }
-    for (int l = threadIdx.x; l < mloc; l += NT) {  // divide by the eigenvalues of I - alpha Lap_h
-      int i[3];
-      local_index<DIM>(q, l, i);
-      double lam = 0.0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) lam += q.mu[a][i[a]];
-      src[l] = src[l] / (1.0 - q.alpha * lam);
-    }
+    for (int l = threadIdx.x; l < mloc; l += NT)  // divide by the eigenvalues of I - alpha Lap_h
+      src[l] *= __ldg(q.inv_eig + l);
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {  // back (S is its own inverse)
@@ -409,15 +418,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT) cn_pair_kernel(c
       const double *row = S + g0 * m0;
       double acc = 0.0;
       for (int j = 0; j < m0; ++j) acc = fma(__ldg(row + j), at(rs, j, w), acc);
-      if (scale) {
-        int i[3], gi[3];
-        double xc[3];
-        node(l, i, gi, xc);
-        double lam = 0.0;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) lam += q.mu[a][i[a]];
-        acc = acc / (1.0 - q.alpha * lam);
-      }
+      if (scale) acc *= __ldg(q.inv_eig + r0 * plane + l);
       mine[rd * cap + l] = acc;
     }
   };
@@ -798,6 +799,8 @@ int grt_pdd_solve_range(grt_ctx *c, const grt_pdd_grid *g, int64_t sub_begin, in
     doff[a] = dsz;
     dsz += (long long)q.m[a] * q.m[a] + q.m[a];
   }
+  const long long ioff = dsz;  // the inverse-eigenvalue table follows the DST tables
+  dsz += q.mloc;
   const size_t vec_bytes = 4 * (size_t)q.mloc * sizeof(double);
   q.use_smem = vec_bytes <= kPddSmemBytes ? 1 : 0;
   const long long vsz = q.use_smem ? 0 : nsub * 4 * (long long)q.mloc;
@@ -811,6 +814,7 @@ int grt_pdd_solve_range(grt_ctx *c, const grt_pdd_grid *g, int64_t sub_begin, in
     q.S[a] = a < d ? Dt + doff[a] : nullptr;
     q.mu[a] = a < d ? Dt + doff[a] + (long long)q.m[a] * q.m[a] : nullptr;
   }
+  q.inv_eig = Dt + ioff;
   q.u_out = d_u_out;
   for (int a = 0; a < 3; ++a) q.B[a] = a < d ? Bb + boff[a] : nullptr;
 
@@ -823,6 +827,9 @@ int grt_pdd_solve_range(grt_ctx *c, const grt_pdd_grid *g, int64_t sub_begin, in
   for (int a = 0; a < d; ++a)
     grt::dst_tables_kernel<<<(q.m[a] * q.m[a] + 127) / 128, 128, 0, s>>>(q.m[a], q.h[a], Dt + doff[a],
                                                                           Dt + doff[a] + (long long)q.m[a] * q.m[a]);
+  grt::inv_eig_kernel<<<grid_for(q.mloc), 256, 0, s>>>(d, q.m[0], d > 1 ? q.m[1] : 1, d > 2 ? q.m[2] : 1, q.alpha,
+                                                      q.mu[0], d > 1 ? q.mu[1] : q.mu[0], d > 2 ? q.mu[2] : q.mu[0],
+                                                      Dt + ioff);
   // weights: time axis (t_nodes + 1 uniform levels over [0, T]) and every space axis
   grt::spline_weights_kernel<<<1, 256, 0, s>>>(tn, 0.0, g->T / g->t_nodes, g->nsteps, tg, W);
   for (int a = 0; a < d; ++a)
