@@ -710,7 +710,9 @@ def gpu_arm(args) -> int:
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "finite_output": finite,
     }
-    if not args.no_workloads:
+    # the single-GPU lines (other workloads, serving, CPU baseline) are measured at N = 1 only: at N > 1
+    # the run is about the sharded main workload, and the other GPUs would idle meanwhile
+    if not args.no_workloads and world == 1:
         line["workloads"] = {
             "uneven_2d": dict(workload_bench(grt, local, "uneven_2d", 5), description=(
                 "2-D u_t = Lap u + u^2, u0 = 1.5 + 0.5 cos x cos y, 4096 points on 64 interface segments of the 8x8 "
@@ -727,7 +729,7 @@ def gpu_arm(args) -> int:
                 "Example 5: 2-D u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (variable coefficient), u0 = e^{-x^2/4}/sqrt(4 pi), "
                 "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, binary trees q = 2/3, K = 8, [4/4]")),
         }
-    if not args.no_serving:
+    if not args.no_serving and world == 1:
         line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,
                                         float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
     if world == 1 and not args.no_cpu_baseline:
