@@ -521,14 +521,22 @@ def gpu_arm(args) -> int:
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
+    # NCCL across the node's GPUs; GRT_DIST_BACKEND=gloo runs the same path with host-side collectives
+    # (used to exercise the multi-rank code on a single GPU: ranks share it, no kernel waits on another)
+    backend = os.environ.get("GRT_DIST_BACKEND", "nccl")
+    gpu = local % max(torch.cuda.device_count(), 1)
     if world > 1:
         import torch.distributed as dist_mod
 
         dist = dist_mod
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
+        torch.cuda.set_device(gpu)
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", gpu))
+        else:
+            dist.init_process_group(backend)
+    dev = torch.device("cuda", gpu)
     torch.cuda.set_device(dev)
+    red_dev = dev if backend == "nccl" else torch.device("cpu")
 
     import __graft_entry__
 
@@ -544,7 +552,7 @@ def gpu_arm(args) -> int:
     n, K, L, M = wl["x"].shape[0], wl["K"], wl["L"], wl["M"]
     point_base = rank * n
     trees_per_step = float(np.sum(wl["ntrees"]))
-    ctx = grt.grt_create(wl["problem"], local)
+    ctx = grt.grt_create(wl["problem"], gpu)
     plan = grt.grt_plan_create(ctx, wl["ntrees"], K, L, M)
     grt.grt_plan_set_timing(plan, True)
     x = torch.from_numpy(wl["x"]).to(dev)
@@ -604,7 +612,7 @@ def gpu_arm(args) -> int:
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
     if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=red_dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     time.sleep(0.3)
@@ -645,7 +653,7 @@ def gpu_arm(args) -> int:
         grt.grt_solve(ctx, xh, th, nth, K, L, M, wl["seed"], point_base, want_coef=False, want_se=False, out=out)
     e2e_s = max(time.perf_counter() - t0, 1e-9)
     if dist is not None:
-        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=red_dev)
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e_s = float(te.item())
     same = bool(np.array_equal(uh, u_host)) if e2e_steps else None
@@ -714,23 +722,23 @@ def gpu_arm(args) -> int:
     # the run is about the sharded main workload, and the other GPUs would idle meanwhile
     if not args.no_workloads and world == 1:
         line["workloads"] = {
-            "uneven_2d": dict(workload_bench(grt, local, "uneven_2d", 5), description=(
+            "uneven_2d": dict(workload_bench(grt, gpu, "uneven_2d", 5), description=(
                 "2-D u_t = Lap u + u^2, u0 = 1.5 + 0.5 cos x cos y, 4096 points on 64 interface segments of the 8x8 "
                 "split of [0,8]^2, t ~ U[0.1, 2], budgets log-uniform in [1e3, 1e6] (5.9e8 trees), K = 16, [8/8]")),
-            "pdd_3d": dict(workload_bench(grt, local, "pdd_3d", 3), description=(
+            "pdd_3d": dict(workload_bench(grt, gpu, "pdd_3d", 3), description=(
                 "3-D u_t = 0.1 Lap u + u - u^3, u0 = prod tanh(x_i - 2), 9 interior planes x 32^2 nodes of the "
                 "4x4x4 split of [0,4]^3, t = 1, 1e5 trees per point (9.2e8 trees), K = 12, [6/6]")),
-            "pdd_3d_pipeline": pdd_bench(grt, local, 3),
-            "drift_2d": dict(workload_bench(grt, local, "drift_2d", 10), description=(
+            "pdd_3d_pipeline": pdd_bench(grt, gpu, 3),
+            "drift_2d": dict(workload_bench(grt, gpu, "drift_2d", 10), description=(
                 "general drift and diffusion: u_t = sum_i (s_i^2/2) d_ii u - kappa_i x_i d_i u + u^2 - u, kappa = (1, 0.5), "
                 "s = (1, 0.7) (OU paths by Euler-Maruyama, 8 steps per segment), u0 = exp(-|x - (0.5,-0.3)|^2/1.28), "
                 "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, K = 8, [4/4]")),
-            "var_coef_2d": dict(workload_bench(grt, local, "var_coef_2d", 10), description=(
+            "var_coef_2d": dict(workload_bench(grt, gpu, "var_coef_2d", 10), description=(
                 "Example 5: 2-D u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (variable coefficient), u0 = e^{-x^2/4}/sqrt(4 pi), "
                 "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, binary trees q = 2/3, K = 8, [4/4]")),
         }
     if not args.no_serving and world == 1:
-        line["serving"] = serving_bench(grt, local, value / world, args.serving_requests, args.plain_requests,
+        line["serving"] = serving_bench(grt, gpu, value / world, args.serving_requests, args.plain_requests,
                                         float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")),
