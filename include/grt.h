@@ -226,6 +226,17 @@ int grt_plan_graph_launch(grt_plan *plan, void *stream);
 /* Release a plan.  NULL is ignored. */
 void grt_plan_destroy(grt_plan *plan);
 
+/* Per-result statistical error of the Pade value (Sec. 2.4: the Pade value is
+ * Lipschitz in the coefficients, Wuytack bound): err_i = sqrt(sum_j (du/da_j
+ * SE_j)^2) over j = 0..L+M, the derivatives by central differences of the FP64
+ * approximant with steps h_j = 1e-6 max(|a_j|, 1e-12 max_i |a_i|) -- a
+ * first-order estimate of the spread of u over independent tree samples.
+ * d_coef, d_se: DEVICE [n][K+1] (as written by the solves); d_err: DEVICE [n];
+ * +inf where an evaluation is not finite.  Enqueued on `stream` (NULL =
+ * legacy default stream).  GRT_EINVAL for bad sizes or NULL arrays. */
+int grt_pade_error(grt_ctx *ctx, int64_t n, int K, int L, int M, const double *d_coef, const double *d_se,
+                   double *d_err, void *stream);
+
 /* The FP64 [L/M] Pade stage alone (Sec. 2.1 end, Sec. 2.4), on the GPU, for
  * n series given on the HOST as coef [n][K+1] (K >= L + M).  Writes u_out [n]
  * and status_out [n] (may be NULL; only the PADE_* bits are set). */

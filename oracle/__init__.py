@@ -259,3 +259,34 @@ def solve(pb: dict, x, t, ntrees, K: int, L: int, M: int, seed: int, point_base:
         raise ValueError("oracle_solve: invalid arguments")
     return dict(u=u, coef=coef, se=se, status=st, s1=s1, s2=s2, sa=sa, cnt=cnt, nodes=nodes,
                 nthreads=int(min(nthreads, max(n, 1))))
+
+
+def pade_error(coef, se, L: int, M: int) -> np.ndarray:
+    """Per-result first-order error of the [L/M] Pade value: sqrt(sum_j (du/da_j SE_j)^2), j = 0..L+M,
+    the derivatives by central differences of this oracle's Pade with steps
+    h_j = 1e-6 max(|a_j|, 1e-12 max_i |a_i|) (the Pade value is Lipschitz in the coefficients,
+    Sec. 2.4); +inf where an evaluation is not finite."""
+    coef = np.atleast_2d(np.asarray(coef, np.float64))
+    se = np.atleast_2d(np.asarray(se, np.float64))
+    out = np.zeros(coef.shape[0])
+    nn = L + M
+    for i in range(coef.shape[0]):
+        a = coef[i, : nn + 1].copy()
+        amax = np.abs(a).max() if a.size else 0.0
+        acc, ok = 0.0, True
+        for j in range(nn + 1):
+            s = se[i, j]
+            if s == 0.0:
+                continue
+            h = 1e-6 * max(abs(a[j]), 1e-12 * amax, 1e-300)
+            ap, am = a.copy(), a.copy()
+            ap[j] += h
+            am[j] -= h
+            up, _, _ = pade(ap, L, M)
+            um, _, _ = pade(am, L, M)
+            d = (up - um) / (2.0 * h) * s
+            if not np.isfinite(d):
+                ok = False
+            acc += d * d
+        out[i] = np.sqrt(acc) if ok else np.inf
+    return out

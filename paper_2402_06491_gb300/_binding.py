@@ -103,6 +103,7 @@ def _load():
         "grt_plan_graph_launch": ([_vp, _vp], i32),
         "grt_plan_destroy": ([_vp], None),
         "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
+        "grt_pade_error": ([_vp, i64, i32, i32, i32, _vp, _vp, _vp, _vp], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
         "grt_solve_noalloc": ([_vp, i64, _vp, _vp, u64p, i32, i32, i32, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
         "grt_server_create": ([i32, u64, u64, _P(_vp)], i32),
@@ -397,6 +398,20 @@ def grt_pade(ctx: Context, coef, L: int, M: int):
     return u, st
 
 
+def grt_pade_error(ctx: Context, coef, se, L: int, M: int, err, stream=None) -> None:
+    """Per-result first-order error of the Pade value from the coefficient standard errors.
+    coef, se: device [n][K+1] float64; err: device [n] float64 (torch tensors or raw addresses)."""
+    lib = _load()
+    n = int(coef.shape[0]) if hasattr(coef, "shape") else None
+    K = int(coef.shape[1]) - 1 if hasattr(coef, "shape") else None
+    if n is None:
+        raise ValueError("coef must carry its shape (a torch tensor)")
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.grt_pade_error(ctx.handle, n, K, L, M, _devptr(coef), _devptr(se), _devptr(err), sh), ctx.handle)
+
+
 def grt_trees(ctx: Context, x, t: float, point_index: int, first_tree: int, ntrees: int, K: int, seed: int) -> dict:
     """Per-tree records (order, weight, nodes, topology hash) of one point's trees, from the GPU."""
     lib = _load()
@@ -598,6 +613,6 @@ EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_pla
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
             "grt_plan_set_config", "grt_plan_get_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
-            "grt_pade", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
+            "grt_pade", "grt_pade_error", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",
             "grt_pdd_points", "grt_pdd_solve", "grt_pdd_solve_range"]

@@ -695,6 +695,19 @@ void grt_plan_destroy(grt_plan *p) {
   delete p;
 }
 
+int grt_pade_error(grt_ctx *c, int64_t n, int K, int L, int M, const double *d_coef, const double *d_se,
+                   double *d_err, void *stream) {
+  if (!c) return GRT_EINVAL;
+  if (n < 0 || n > 0x7FFFFFFFll) return c->set_error(GRT_EINVAL, "n must be in [0, 2^31)");
+  if (K < 0 || K > GRT_MAX_K || L < 0 || M < 0 || L + M > K)
+    return c->set_error(GRT_EINVAL, "need 0 <= K <= 16, L, M >= 0, L + M <= K");
+  if (n == 0) return GRT_OK;
+  if (!d_coef || !d_se || !d_err) return c->set_error(GRT_EINVAL, "coef, se and err must be non-NULL");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  GRT_CUDA(c, grt::launch_pade_error((int)n, K, L, M, d_coef, d_se, d_err, (cudaStream_t)stream));
+  return GRT_OK;
+}
+
 int grt_pade(grt_ctx *c, int64_t n, int K, int L, int M, const double *coef, double *u_out, int32_t *status_out) {
   if (!c) return GRT_EINVAL;
   if (n < 0 || n > 0x7FFFFFFFll) return c->set_error(GRT_EINVAL, "n must be in [0, 2^31)");

@@ -3,6 +3,7 @@
 // the FP64 [L/M] Pade approximant at eps = 1 (Sec. 2.1 end, Sec. 2.4).
 #include "grt_device.cuh"
 #include "grt_launch.h"
+#include <math_constants.h>
 
 namespace grt {
 
@@ -340,6 +341,47 @@ __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, doub
   int st = 0;
   u[i] = pade_value(a, L, M, &st);
   if (status) status[i] = st;
+}
+
+// First-order statistical error of the Pade value: with the coefficients' standard errors
+// SE_j, err = sqrt(sum_j (du/da_j SE_j)^2), du/da_j by central differences of the FP64
+// approximant with steps h_j = 1e-6 max(|a_j|, 1e-12 max_i |a_i|) (the sensitivity the
+// Wuytack bound of Sec. 2.4 speaks of, made per result).  +inf when an evaluation fails.
+__global__ void pade_error_kernel(int n, int K, int L, int M, const double *coef, const double *se, double *err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nn = L + M;
+  double a[kMaxK + 1];
+  double amax = 0.0;
+  for (int j = 0; j <= nn; ++j) {
+    a[j] = coef[(size_t)i * (K + 1) + j];
+    amax = fmax(amax, fabs(a[j]));
+  }
+  double acc = 0.0;
+  bool ok = true;
+  for (int j = 0; j <= nn; ++j) {
+    const double s = se[(size_t)i * (K + 1) + j];
+    if (s == 0.0) continue;
+    const double h = 1e-6 * fmax(fmax(fabs(a[j]), 1e-12 * amax), 1e-300);
+    const double aj = a[j];
+    int st = 0;
+    a[j] = aj + h;
+    const double up = pade_value(a, L, M, &st);
+    a[j] = aj - h;
+    const double um = pade_value(a, L, M, &st);
+    a[j] = aj;
+    const double d = (up - um) / (2.0 * h) * s;
+    if (!isfinite(d)) ok = false;
+    acc += d * d;
+  }
+  err[i] = ok ? sqrt(acc) : CUDART_INF;
+}
+
+cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, const double *se, double *err,
+                              cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  pade_error_kernel<<<(n + 127) / 128, 128, 0, stream>>>(n, K, L, M, coef, se, err);
+  return cudaGetLastError();
 }
 
 template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParams &f, cudaStream_t stream) {

@@ -107,3 +107,21 @@ def test_degenerate_cases():
     assert abs(u - a.sum()) < 1e-16 and st == 0
     with pytest.raises(ValueError):
         oracle.pade(np.zeros(17), 9, 8)
+
+
+def test_pade_error_closed_forms(oracle_mod):
+    """The per-result error helper on approximants with closed-form derivatives:
+    [0/0] u = a0; [1/0] u = a0 + a1; [0/1] u = a0^2 / (a0 - a1)."""
+    import numpy as np
+
+    a = np.array([[0.7, 0.3, 0.0], [1.2, -0.4, 0.0]])
+    se = np.array([[0.01, 0.02, 0.0], [0.03, 0.005, 0.0]])
+    e00 = oracle_mod.pade_error(a, se, 0, 0)
+    assert np.allclose(e00, se[:, 0], rtol=1e-9)
+    e10 = oracle_mod.pade_error(a, se, 1, 0)
+    assert np.allclose(e10, np.hypot(se[:, 0], se[:, 1]), rtol=1e-8)
+    e01 = oracle_mod.pade_error(a, se, 0, 1)
+    a0, a1 = a[:, 0], a[:, 1]
+    d0 = (a0 * a0 - 2.0 * a0 * a1) / (a0 - a1) ** 2
+    d1 = a0 * a0 / (a0 - a1) ** 2
+    assert np.allclose(e01, np.hypot(d0 * se[:, 0], d1 * se[:, 1]), rtol=1e-6)

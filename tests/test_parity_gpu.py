@@ -386,3 +386,30 @@ def test_full_size_workloads_sampled_points(grt, name, ctol):
                          wl["M"], wl["seed"], point_base=i)
         gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
         _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], ctol=ctol, L=wl["L"], M=wl["M"])
+
+
+def test_pade_error_parity_and_calibration(grt):
+    """grt_pade_error against the oracle's helper on the same coefficients, and calibration: over
+    independent seeds the spread of u matches the first-order error of a single solve."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.subsample(workloads.workload_sin_2d(), 6, ntrees=4000, stride=83)
+    K, L, M = wl["K"], wl["L"], wl["M"]
+    ctx = grt.grt_create(wl["problem"], 0)
+    us, errs = [], []
+    for seed in range(40):
+        g = grt.grt_solve(ctx, wl["x"], wl["t"], wl["ntrees"], K, L, M, seed)
+        coef = torch.from_numpy(g["coef"]).cuda()
+        se = torch.from_numpy(g["se"]).cuda()
+        err = torch.empty(coef.shape[0], dtype=torch.float64, device="cuda")
+        grt.grt_pade_error(ctx, coef, se, L, M, err)
+        e = err.cpu().numpy()
+        if seed == 0:
+            eo = oracle.pade_error(g["coef"], g["se"], L, M)
+            assert np.allclose(e, eo, rtol=1e-6, atol=0), (e, eo)
+        us.append(g["u"])
+        errs.append(e)
+    ctx.close()
+    spread = np.std(np.array(us), axis=0, ddof=1)
+    est = np.mean(np.array(errs), axis=0)
+    ratio = spread / est
+    assert np.all((ratio > 0.55) & (ratio < 1.8)), (spread, est)
