@@ -635,6 +635,18 @@ def gpu_arm(args) -> int:
     # result must at least be finite
     u_host = u.cpu().numpy()
     finite = bool(np.all(np.isfinite(u_host)))
+    # each result's statistical error: one more execute with standard errors, then grt_pade_error
+    se_d = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    grt.grt_plan_execute(plan, x, t, wl["seed"], point_base, u, coef, se_d, status, stream=stream)
+    err_d = torch.empty(n, dtype=torch.float64, device=dev)
+    grt.grt_pade_error(ctx, coef, se_d, L, M, err_d, stream=stream)
+    stream.synchronize()
+    err_h = err_d.cpu().numpy()
+    rel_err = err_h / np.maximum(np.abs(u_host), 1e-300)
+    stat_err = {"median_abs": float(np.median(err_h)), "max_abs": float(np.max(err_h)),
+                "median_rel": float(np.median(rel_err)),
+                "note": "first-order spread of the Pade value from the coefficients' standard errors "
+                        "(grt_pade_error), per point at this run's tree budget"}
 
     # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result
     e2e_steps = 0 if args.no_e2e else max(args.steps, 1)
@@ -716,6 +728,7 @@ def gpu_arm(args) -> int:
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
+        "statistical_error": stat_err,
         "finite_output": finite,
     }
     # the single-GPU lines (other workloads, serving, CPU baseline) are measured at N = 1 only: at N > 1
