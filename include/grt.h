@@ -226,6 +226,15 @@ int grt_plan_graph_launch(grt_plan *plan, void *stream);
 /* Release a plan.  NULL is ignored. */
 void grt_plan_destroy(grt_plan *plan);
 
+/* Cancellation factor kappa_n = SA_n / |S1_n| (sum of |W| over the sum of W of the
+ * trees of order n) of every point of the plan's last execution, from its
+ * resident per-chunk sums: a kappa far above 1 says that order's mean is a
+ * small difference of large weights (its relative statistical error grows
+ * with kappa).  d_kappa: DEVICE [n][K+1]; 0 where no tree has that order, +inf
+ * where S1 = 0 < SA.  Enqueued on `stream` (NULL = legacy default stream),
+ * after the execution it reads (same stream, or ordered by the caller). */
+int grt_plan_kappa(grt_plan *plan, double *d_kappa, void *stream);
+
 /* Per-result statistical error of the Pade value (Sec. 2.4: the Pade value is
  * Lipschitz in the coefficients, Wuytack bound): err_i = sqrt(sum_j (du/da_j
  * SE_j)^2) over j = 0..L+M, the derivatives by central differences of the FP64

@@ -104,6 +104,7 @@ def _load():
         "grt_plan_destroy": ([_vp], None),
         "grt_pade": ([_vp, i64, i32, i32, i32, f64p, f64p, i32p], i32),
         "grt_pade_error": ([_vp, i64, i32, i32, i32, _vp, _vp, _vp, _vp], i32),
+        "grt_plan_kappa": ([_vp, _vp, _vp], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
         "grt_solve_noalloc": ([_vp, i64, _vp, _vp, u64p, i32, i32, i32, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
         "grt_server_create": ([i32, u64, u64, _P(_vp)], i32),
@@ -398,6 +399,15 @@ def grt_pade(ctx: Context, coef, L: int, M: int):
     return u, st
 
 
+def grt_plan_kappa(plan: Plan, kappa, stream=None) -> None:
+    """Cancellation factors SA_n / |S1_n| of the plan's last execution into the device buffer kappa [n][K+1]."""
+    lib = _load()
+    sh = None
+    if stream is not None:
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.grt_plan_kappa(plan.handle, _devptr(kappa), sh), plan.ctx.handle)
+
+
 def grt_pade_error(ctx: Context, coef, se, L: int, M: int, err, stream=None) -> None:
     """Per-result first-order error of the Pade value from the coefficient standard errors.
     coef, se: device [n][K+1] float64; err: device [n] float64 (torch tensors or raw addresses)."""
@@ -613,6 +623,6 @@ EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_pla
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
             "grt_plan_set_config", "grt_plan_get_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
-            "grt_pade", "grt_pade_error", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
+            "grt_pade", "grt_pade_error", "grt_plan_kappa", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",
             "grt_pdd_points", "grt_pdd_solve", "grt_pdd_solve_range"]

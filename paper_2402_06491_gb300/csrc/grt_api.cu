@@ -695,6 +695,18 @@ void grt_plan_destroy(grt_plan *p) {
   delete p;
 }
 
+int grt_plan_kappa(grt_plan *p, double *d_kappa, void *stream) {
+  if (!p) return GRT_EINVAL;
+  grt_ctx *c = p->ctx;
+  if (p->n < 0) return c->set_error(GRT_EINVAL, "plan has no valid layout");
+  if (p->n == 0) return GRT_OK;
+  if (!d_kappa) return c->set_error(GRT_EINVAL, "kappa must be non-NULL");
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  GRT_CUDA(c, grt::launch_kappa((int)p->n, p->K, p->chunk_prefix.as<uint32_t>(), p->ntrees.as<uint32_t>(),
+                                p->part.as<double>(), d_kappa, (cudaStream_t)stream));
+  return GRT_OK;
+}
+
 int grt_pade_error(grt_ctx *c, int64_t n, int K, int L, int M, const double *d_coef, const double *d_se,
                    double *d_err, void *stream) {
   if (!c) return GRT_EINVAL;

@@ -377,6 +377,39 @@ __global__ void pade_error_kernel(int n, int K, int L, int M, const double *coef
   err[i] = ok ? sqrt(acc) : CUDART_INF;
 }
 
+// Cancellation factor kappa_n = SA_n / |S1_n| (Sec. 2.4: the Monte Carlo mean of a_n is a
+// difference of weights of both signs) of each (point, order) from the resident per-chunk
+// partial sums of a one-shot solve (part [chunk][4][K+2]: S1, S2, SA, count rows), summed over the
+// point's chunks in chunk order with compensation exactly as the binning's last block sums S1.
+// 0 where SA = 0 (no tree of that order), +inf where S1 = 0 < SA.
+__global__ void kappa_kernel(int n, int K, const uint32_t *__restrict__ chunk_prefix,
+                             const uint32_t *__restrict__ ntrees, const double *__restrict__ part,
+                             double *__restrict__ kappa) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int R = K + 2;
+  if (e >= n * (K + 1)) return;
+  const int pt = e / (K + 1), r = e % (K + 1);
+  const size_t pstride = (size_t)4 * R;
+  const uint32_t nt = ntrees[pt];
+  const uint32_t nch = nt == 0u ? 1u : (nt + kBinChunk - 1) / kBinChunk;
+  const double *pp = part + (size_t)chunk_prefix[pt] * pstride;
+  double s1 = 0.0, c1 = 0.0, sa = 0.0, ca = 0.0;
+  for (uint32_t k = 0; k < nch; ++k) {
+    kahan_add(s1, c1, pp[(size_t)k * pstride + r]);
+    kahan_add(sa, ca, pp[(size_t)k * pstride + 2 * R + r]);
+  }
+  const double S1 = s1 - c1, SA = sa - ca;
+  kappa[e] = SA == 0.0 ? 0.0 : (S1 == 0.0 ? CUDART_INF : SA / fabs(S1));
+}
+
+cudaError_t launch_kappa(int n, int K, const uint32_t *chunk_prefix, const uint32_t *ntrees, const double *part,
+                         double *kappa, cudaStream_t stream) {
+  const long long total = (long long)n * (K + 1);
+  if (total <= 0) return cudaSuccess;
+  kappa_kernel<<<(unsigned)((total + 127) / 128), 128, 0, stream>>>(n, K, chunk_prefix, ntrees, part, kappa);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, const double *se, double *err,
                               cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;

@@ -43,6 +43,8 @@ struct WalkConfig {
 
 cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms,
                         cudaStream_t stream);
+cudaError_t launch_kappa(int n, int K, const uint32_t *chunk_prefix, const uint32_t *ntrees, const double *part,
+                         double *kappa, cudaStream_t stream);
 cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, const double *se, double *err,
                               cudaStream_t stream);
 cudaError_t launch_walk_feat(bool fp64, int dim, int strategy, int feat, const WalkParams &p, const WalkConfig &cfg,
