@@ -38,24 +38,34 @@ WORKLOAD = "sin_2d"
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_GB300 = 152
 ISSUE_PER_SM_PER_CLK = 4 * 32   # 4 schedulers x 1 warp-instruction x 32 threads
+FP32_WEIGHT_RTOL = 3e-5        # per-tree FP32 weight vs its FP64 value (the per-tree parity bound)
 
 
 def _walk_profile():
-    """(DRAM bytes per full-size walk launch, issue-slot utilisation) from the committed ncu
-    summary, or (None, None) when the walk kernel's sources changed since that capture."""
+    """(DRAM bytes per full-size walk launch, ncu figures of the walk kernel) from the committed
+    ncu summary, or (None, None) when the walk kernel's sources changed since that capture."""
     import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", "walk_kernel_sin2d.md")).read()
         want = re.search(r"source_sha256_16: ([0-9a-f]+)", text).group(1)
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
-        m = re.search(r"issue_active_pct: ([0-9.]+)", text)
-        issue = float(m.group(1)) / 100.0 if m else None
+
+        def num(key):
+            m = re.search(key + r": ([0-9.]+)", text)
+            return float(m.group(1)) if m else None
+
+        issue, alu, fma, lanes = (num("issue_active_pct"), num("alu_pipe_pct"), num("fma_pipe_pct"),
+                                  num("active_lanes_per_inst"))
+        figs = {"issue_active": issue / 100.0 if issue is not None else None,
+                "alu_pipe": alu / 100.0 if alu is not None else None,
+                "fma_pipe": fma / 100.0 if fma is not None else None,
+                "lane_efficiency": lanes / 32.0 if lanes is not None else None}
         h = hashlib.sha256()
         for f in ("grt_device.cuh", "grt_walk.cuh"):
             with open(os.path.join(ROOT, "paper_2402_06491_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
-        return (traffic, issue) if h.hexdigest()[:16] == want else (None, None)
+        return (traffic, figs) if h.hexdigest()[:16] == want else (None, None)
     except Exception:
         return None, None
 
@@ -647,6 +657,37 @@ def gpu_arm(args) -> int:
                 "median_rel": float(np.median(rel_err)),
                 "note": "first-order spread of the Pade value from the coefficients' standard errors "
                         "(grt_pade_error), per point at this run's tree budget"}
+    # FP32 rounding of each result.  Every tree weight is within eps = 3e-5 of its FP64 value
+    # (per-tree parity), so S1_n moves by at most eps SA_n: |da_n| <= eps kappa_n |a_n| with
+    # kappa_n = SA_n/|S1_n| (worst case: all trees' errors of one sign).  Rounding errors of
+    # independent trees add like noise instead, sqrt(sum W^2) eps = eps sqrt(S2_n): da_n ~ eps
+    # sqrt(SE_n^2 + a_n^2/N).  Both propagate through the Pade by its first-order sensitivities
+    # (grt_pade_error; sqrt(L+M+1) x its quadrature sum bounds the linear sum of the worst case).
+    kap_d = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    grt.grt_plan_kappa(plan, kap_d, stream=stream)
+    stream.synchronize()
+    coef_h, kap_h, se_h = coef.cpu().numpy(), kap_d.cpu().numpy(), se_d.cpu().numpy()
+    Nt = np.maximum(np.asarray(wl["ntrees"], np.float64), 1.0)[:, None]
+    da_worst = np.where(np.isfinite(kap_h), FP32_WEIGHT_RTOL * kap_h * np.abs(coef_h), 0.0)
+    da_noise = FP32_WEIGHT_RTOL * np.sqrt(se_h * se_h + coef_h * coef_h / Nt)
+    scale = np.maximum(np.abs(u_host), np.abs(coef_h).sum(axis=1))
+    rel = {}
+    for name, da, mult in (("worst", da_worst, math.sqrt(L + M + 1)), ("noise", da_noise, 1.0)):
+        da_dev = torch.from_numpy(np.ascontiguousarray(da)).to(dev)
+        rb_d = torch.empty(n, dtype=torch.float64, device=dev)
+        grt.grt_pade_error(ctx, coef, da_dev, L, M, rb_d, stream=stream)
+        stream.synchronize()
+        rel[name] = rb_d.cpu().numpy() * mult / np.maximum(scale, 1e-300)
+    over = np.where(~(rel["worst"] <= 1e-5))[0]
+    fin = np.isfinite(kap_h)
+    fp32_bound = {
+        "worst_case_median_rel": float(np.median(rel["worst"])), "worst_case_max_rel": float(np.max(rel["worst"])),
+        "worst_case_over_1e-5": int(over.size), "worst_case_over_1e-5_first": [int(i) + point_base for i in over[:20]],
+        "independent_median_rel": float(np.median(rel["noise"])), "independent_max_rel": float(np.max(rel["noise"])),
+        "kappa_max": float(np.max(kap_h[fin])) if fin.any() else None,
+        "note": "FP32 walk rounding on each Pade value relative to max(|u|, sum |a_n|), per-tree weights within "
+                "3e-5 (tested): worst case 3e-5 kappa_n |a_n| per coefficient (kappa_n = SA_n/|S1_n|, "
+                "grt_plan_kappa), and independent per-tree errors 3e-5 sqrt(SE_n^2 + a_n^2/N)"}
 
     # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result
     e2e_steps = 0 if args.no_e2e else max(args.steps, 1)
@@ -708,10 +749,12 @@ def gpu_arm(args) -> int:
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
             "traffic": walk_prof[0] if not args.trees else None,
-            "issue_active_ncu": walk_prof[1],
+            "issue_active_ncu": walk_prof[1]["issue_active"] if walk_prof[1] else None,
+            "ncu": walk_prof[1],
             "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case; "
                           "profiles/walk_kernel_sin2d.md): the hardware's SM issue-slot utilisation, "
-                          "beside the stricter algorithmic fraction `frac`",
+                          "beside the stricter algorithmic fraction `frac`; `ncu` adds the ALU and FMA "
+                          "pipe utilisation and the warp-divergence efficiency (active lanes / 32)",
             "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md); "
                             "algorithmic bytes are the 5 B/tree records = 256 MB written",
             "kernel": "walk_kernel<float,2,B> (persistent tree walk)",
@@ -729,6 +772,7 @@ def gpu_arm(args) -> int:
         "clocks": clocks,
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "statistical_error": stat_err,
+        "fp32_rounding_bound": fp32_bound,
         "finite_output": finite,
     }
     # the single-GPU lines (other workloads, serving, CPU baseline) are measured at N = 1 only: at N > 1
