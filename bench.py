@@ -62,7 +62,7 @@ def _walk_profile():
                 "fma_pipe": fma / 100.0 if fma is not None else None,
                 "lane_efficiency": lanes / 32.0 if lanes is not None else None}
         h = hashlib.sha256()
-        for f in ("grt_device.cuh", "grt_walk.cuh"):
+        for f in ("grt_device.cuh", "grt_walk.cuh", "grt_walk_u0.cu"):
             with open(os.path.join(ROOT, "paper_2402_06491_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
         return (traffic, figs) if h.hexdigest()[:16] == want else (None, None)

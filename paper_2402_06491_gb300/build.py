@@ -18,8 +18,13 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libgrt.so")
 
-SOURCES = ["grt_api.cu", "grt_walk.cu", "grt_walk_feat.cu", "grt_trees.cu", "grt_finalize.cu", "grt_server.cu",
-           "grt_pdd.cu"]
+# (source, object name, extra nvcc flags): grt_walk_u0.cu is compiled once per launch shape
+SOURCES = [("grt_api.cu", "grt_api", []), ("grt_walk.cu", "grt_walk", []), ("grt_walk_feat.cu", "grt_walk_feat", []),
+           ("grt_trees.cu", "grt_trees", []), ("grt_finalize.cu", "grt_finalize", []),
+           ("grt_server.cu", "grt_server", []), ("grt_pdd.cu", "grt_pdd", [])]
+for _w, _s in ((4, 0), (4, 3), (8, 0), (8, 3)):
+    SOURCES.append(("grt_walk_u0.cu", f"grt_walk_u0_w{_w}s{_s}",
+                    [f"-DGRT_U0_FN=launch_walk_u0_w{_w}s{_s}", f"-DGRT_U0_WARPS={_w}", f"-DGRT_U0_SLEV={_s}"]))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
@@ -55,9 +60,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD_DIR, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
-    def compile_one(src: str):
-        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(entry):
+        src, name, defs = entry
+        obj = os.path.join(BUILD_DIR, name + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -251,11 +251,13 @@ __device__ __forceinline__ void initial_data_base(const WalkParams &p, const dou
 //   LOGISTIC  c0, A, x0, -1/width
 //   GAUSS_AXES c0, A, -w0, -w1, -w2, m0, m1, m2
 //   QUADRATIC  c0, l0, l1, l2, q0, q1, q2
-template <typename Real, int DIM>
+// U0 >= 0 fixes the kind at compile time (the switch folds to its one case);
+// U0 = -1 reads it from the parameters.
+template <typename Real, int DIM, int U0 = -1>
 __device__ __forceinline__ Real initial_data(const WalkParams &p, const Real (&base)[DIM], const Real (&D)[DIM]) {
   using M = Math<Real>;
   const Real c0 = pconst<Real>(p, 0), A = pconst<Real>(p, 1);
-  switch (p.u0_kind) {
+  switch (U0 >= 0 ? U0 : p.u0_kind) {
   case kU0Gauss: {
     Real r2 = Real(0);
 #pragma unroll
@@ -443,7 +445,7 @@ template <typename Real, int DIM> struct NodeOut {
 // `s_factor`, `s_thr` and the caller's arity table are block-shared copies of the tables;
 // x is the displacement from the tree's root, `base` the root's shifted origin
 // and xp the root's coordinates (read only by a variable coefficient).
-template <typename Real, int DIM, int STRAT, int FEAT = 0>
+template <typename Real, int DIM, int STRAT, int FEAT = 0, int U0 = -1>
 __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__restrict__ s_factor,
                                           const uint32_t *__restrict__ s_thr, const Real (&base)[DIM],
                                           const double *__restrict__ xp, const Real (&x)[DIM], Real tau,
@@ -495,26 +497,19 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
   }
 
-  if (leaf) {
-    const Real g = initial_data<Real, DIM>(p, base, o.y);
-    if (STRAT == kStratB) {
-      o.factor = Scalars<Real>::leaf(p) * g;
-    } else {
-      // with no term (f = 0, hence c = 0) there is no clock: the leaf carries g alone
-      const Real lmc = Scalars<Real>::lam_minus_c(p);
-      o.factor = (lmc == Real(0) || p.nterms == 0) ? g : F::exp_scaled(lmc * tau) * g;
-    }
+  // every lane evaluates g (a leaf uses it) and reads its term factor (a split uses it):
+  // the warp runs one convergent body instead of two divergent ones
+  const Real g = initial_data<Real, DIM, U0>(p, base, o.y);
+  const Real tf = s_factor[leaf ? 0 : o.cat];
+  if (STRAT == kStratB) {
+    o.factor = leaf ? Scalars<Real>::leaf(p) * g : tau * tf;
   } else {
-    const Real tf = s_factor[o.cat];
-    if (STRAT == kStratB) {
-      o.factor = tau * tf;
-    } else {
-      const Real lmc = Scalars<Real>::lam_minus_c(p);
-      o.factor = (lmc == Real(0)) ? tf : F::exp_scaled(lmc * S) * tf;
-    }
-    if constexpr ((FEAT & kFeatVarCoef) != 0)
-      if ((p.coef_cat_mask >> o.cat) & 1u) o.factor *= coef_gamma<Real, DIM>(p, xp, o.y, o.tau_c);
+    const Real lmc = Scalars<Real>::lam_minus_c(p);
+    const Real e = lmc == Real(0) ? Real(1) : F::exp_scaled(lmc * (leaf ? tau : S));
+    o.factor = leaf ? ((p.nterms == 0) ? g : e * g) : e * tf;
   }
+  if constexpr ((FEAT & kFeatVarCoef) != 0)
+    if (!leaf && ((p.coef_cat_mask >> o.cat) & 1u)) o.factor *= coef_gamma<Real, DIM>(p, xp, o.y, o.tau_c);
 }
 
 }  // namespace grt

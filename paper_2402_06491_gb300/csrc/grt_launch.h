@@ -43,6 +43,16 @@ struct WalkConfig {
 
 cudaError_t launch_walk(bool fp64, int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms,
                         cudaStream_t stream);
+// The FP32 featureless walk, one instantiation per kind of initial data, in each launch shape
+// (w: warps per block, s: stack levels in shared memory, 0 = all); grt_walk_u0.cu.
+#define GRT_U0_DECL(name)                                                                                  \
+  cudaError_t name(int dim, int strategy, const WalkParams &p, const WalkConfig &cfg, int num_sms, \
+                   cudaStream_t stream);
+GRT_U0_DECL(launch_walk_u0_w4s0)
+GRT_U0_DECL(launch_walk_u0_w4s3)
+GRT_U0_DECL(launch_walk_u0_w8s0)
+GRT_U0_DECL(launch_walk_u0_w8s3)
+#undef GRT_U0_DECL
 cudaError_t launch_kappa(int n, int K, const uint32_t *chunk_prefix, const uint32_t *ntrees, const double *part,
                          double *kappa, cudaStream_t stream);
 cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, const double *se, double *err,

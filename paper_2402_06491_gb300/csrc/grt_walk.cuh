@@ -1,8 +1,10 @@
 // grt_walk.cuh -- the persistent random-tree walk kernel and the per-tree
 // diagnostic kernel, as templates over the walk precision, the dimension, the
-// strategy, the launch shape and the problem's features (kFeatEuler: Euler-
-// Maruyama paths; kFeatVarCoef: variable coefficients).  Instantiated by
-// grt_walk.cu (no feature: every launch shape), grt_walk_feat.cu (features:
+// strategy, the launch shape, the problem's features (kFeatEuler: Euler-
+// Maruyama paths; kFeatVarCoef: variable coefficients) and optionally the kind
+// of initial data.  Instantiated by grt_walk.cu (no feature: every launch
+// shape), grt_walk_u0.cu (FP32, no feature, 4 warps with the stack in shared
+// memory: one kernel per kind of initial data), grt_walk_feat.cu (features:
 // 4 warps, stack in shared memory) and grt_trees.cu (the diagnostic kernel).
 #pragma once
 //
@@ -66,7 +68,7 @@ __device__ __forceinline__ int find_point(const uint32_t *__restrict__ prefix, i
   return lo;
 }
 
-template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int FEAT = 0>
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int FEAT = 0, int U0 = -1>
 __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Real s_factor[kMaxTerms];
@@ -187,8 +189,8 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
     // pending sibling from the stack (up), or the tree is done.
     ++nodes;
     NodeOut<Real, DIM> o;
-    node_step<Real, DIM, STRAT, FEAT>(p, s_factor, s_thr, base, p.x + (size_t)pidx * DIM, x, tau, id_lo, id_hi, tree,
-                                point, o);
+    node_step<Real, DIM, STRAT, FEAT, U0>(p, s_factor, s_thr, base, p.x + (size_t)pidx * DIM, x, tau, id_lo, id_hi,
+                                          tree, point, o);
     W *= o.factor;
     const bool split = o.cat >= 0;
     Ne += split ? 1 : 0;
@@ -379,10 +381,10 @@ __global__ void trees_kernel(const WalkParams p, double x0_0, double x0_1, doubl
 
 // Launch of one instantiation: grid = SMs x resident blocks (or the configured
 // blocks per SM), no larger than the queue's warps.
-template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int FEAT = 0>
+template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int FEAT = 0, int U0 = -1>
 inline cudaError_t launch_walk_t(const WalkParams &p, const WalkConfig &cfg, int num_sms, cudaStream_t stream) {
   const size_t smem = warp_stack_bytes<Real, DIM>(p.K, SLEV) * WARPS;
-  auto kern = walk_kernel<Real, DIM, STRAT, WARPS, SLEV, FEAT>;
+  auto kern = walk_kernel<Real, DIM, STRAT, WARPS, SLEV, FEAT, U0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
