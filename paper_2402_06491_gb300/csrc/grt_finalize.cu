@@ -347,9 +347,12 @@ __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, doub
 // SE_j, err = sqrt(sum_j (du/da_j SE_j)^2), du/da_j by central differences of the FP64
 // approximant with steps h_j = 1e-6 max(|a_j|, 1e-12 max_i |a_i|) (the sensitivity the
 // Wuytack bound of Sec. 2.4 speaks of, made per result).  +inf when an evaluation fails.
+// One warp per result: lane j <= L+M forms the central difference of coefficient j, and lane 0
+// adds the squared terms in order j = 0, 1, ...
 __global__ void pade_error_kernel(int n, int K, int L, int M, const double *coef, const double *se, double *err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps leave together
   const int nn = L + M;
   double a[kMaxK + 1];
   double amax = 0.0;
@@ -357,24 +360,28 @@ __global__ void pade_error_kernel(int n, int K, int L, int M, const double *coef
     a[j] = coef[(size_t)i * (K + 1) + j];
     amax = fmax(amax, fabs(a[j]));
   }
-  double acc = 0.0;
+  double d2 = 0.0;
   bool ok = true;
-  for (int j = 0; j <= nn; ++j) {
+  if (lane <= nn) {
+    const int j = lane;
     const double s = se[(size_t)i * (K + 1) + j];
-    if (s == 0.0) continue;
-    const double h = 1e-6 * fmax(fmax(fabs(a[j]), 1e-12 * amax), 1e-300);
-    const double aj = a[j];
-    int st = 0;
-    a[j] = aj + h;
-    const double up = pade_value(a, L, M, &st);
-    a[j] = aj - h;
-    const double um = pade_value(a, L, M, &st);
-    a[j] = aj;
-    const double d = (up - um) / (2.0 * h) * s;
-    if (!isfinite(d)) ok = false;
-    acc += d * d;
+    if (s != 0.0) {
+      const double h = 1e-6 * fmax(fmax(fabs(a[j]), 1e-12 * amax), 1e-300);
+      const double aj = a[j];
+      int st = 0;
+      a[j] = aj + h;
+      const double up = pade_value(a, L, M, &st);
+      a[j] = aj - h;
+      const double um = pade_value(a, L, M, &st);
+      const double d = (up - um) / (2.0 * h) * s;
+      ok = isfinite(d);
+      d2 = d * d;
+    }
   }
-  err[i] = ok ? sqrt(acc) : CUDART_INF;
+  const bool all_ok = __all_sync(kFull, ok);
+  double acc = 0.0;
+  for (int j = 0; j <= nn; ++j) acc += __shfl_sync(kFull, d2, j);
+  if (lane == 0) err[i] = all_ok ? sqrt(acc) : CUDART_INF;
 }
 
 // Cancellation factor kappa_n = SA_n / |S1_n| (Sec. 2.4: the Monte Carlo mean of a_n is a
@@ -413,7 +420,7 @@ cudaError_t launch_kappa(int n, int K, const uint32_t *chunk_prefix, const uint3
 cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, const double *se, double *err,
                               cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  pade_error_kernel<<<(n + 127) / 128, 128, 0, stream>>>(n, K, L, M, coef, se, err);
+  pade_error_kernel<<<(unsigned)((n + 3) / 4), 128, 0, stream>>>(n, K, L, M, coef, se, err);  // 4 results per block
   return cudaGetLastError();
 }
 
