@@ -232,7 +232,8 @@ void grt_plan_destroy(grt_plan *plan);
  * small difference of large weights (its relative statistical error grows
  * with kappa).  d_kappa: DEVICE [n][K+1]; 0 where no tree has that order, +inf
  * where S1 = 0 < SA.  Enqueued on `stream` (NULL = legacy default stream),
- * after the execution it reads (same stream, or ordered by the caller). */
+ * after the execution it reads (same stream, or ordered by the caller).
+ * GRT_EINVAL if d_kappa is NULL (n > 0) or the plan has never been executed. */
 int grt_plan_kappa(grt_plan *plan, double *d_kappa, void *stream);
 
 /* Per-result statistical error of the Pade value (Sec. 2.4: the Pade value is

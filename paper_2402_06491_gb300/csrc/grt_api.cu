@@ -48,6 +48,7 @@ struct grt_plan {
   grt::DevBuf work;  // queue head (8 B), 3 u64 counters, then n u32 chunk tickets
   size_t work_bytes = 64;
   cudaStream_t last_stream = nullptr;
+  bool executed = false;  // an execution (or graph replay) has been enqueued: the chunk sums exist
   int launches = 0;
   bool timing = false, timed_last = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -391,6 +392,7 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[2], stream));
   p->timed_last = p->timing;
   p->last_stream = stream;
+  p->executed = true;
   return GRT_OK;
 }
 
@@ -685,6 +687,7 @@ int grt_plan_graph_launch(grt_plan *p, void *stream) {
   GRT_CUDA(c, cudaGraphLaunch(p->graph_exec, (cudaStream_t)stream));
   p->last_stream = (cudaStream_t)stream;
   p->timed_last = p->timing;
+  p->executed = true;
   return GRT_OK;
 }
 
@@ -701,6 +704,7 @@ int grt_plan_kappa(grt_plan *p, double *d_kappa, void *stream) {
   if (p->n < 0) return c->set_error(GRT_EINVAL, "plan has no valid layout");
   if (p->n == 0) return GRT_OK;
   if (!d_kappa) return c->set_error(GRT_EINVAL, "kappa must be non-NULL");
+  if (!p->executed) return c->set_error(GRT_EINVAL, "the plan has not been executed");
   GRT_CUDA(c, cudaSetDevice(c->device));
   GRT_CUDA(c, grt::launch_kappa((int)p->n, p->K, p->chunk_prefix.as<uint32_t>(), p->ntrees.as<uint32_t>(),
                                 p->part.as<double>(), d_kappa, (cudaStream_t)stream));

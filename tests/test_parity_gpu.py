@@ -377,6 +377,8 @@ def test_plan_kappa_matches_oracle_sums(grt, precision):
     u = torch.empty(n, dtype=torch.float64, device=dev)
     coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
     kap = torch.full((n, K + 1), -1.0, dtype=torch.float64, device=dev)
+    with pytest.raises(grt.GrtError):  # no execution yet: no chunk sums to read
+        grt.grt_plan_kappa(plan, kap)
     s = torch.cuda.Stream()
     grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, None, stream=s)
     grt.grt_plan_kappa(plan, kap, stream=s)
