@@ -269,7 +269,7 @@ def reference_arm(args) -> int:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "points_per_s": npts * args.steps / total,
-        "config": {"workload": f"{WORKLOAD} (FP64 CPU oracle, the build's own plain reference; no upstream code exists)",
+        "config": {"workload": f"{WORKLOAD} (FP64 CPU oracle: the plain reference of the method; no upstream code exists)",
                    "points_per_step": npts, "trees_per_point": int(wl["ntrees"][0]), "K": wl["K"], "L": wl["L"],
                    "M": wl["M"], "parallelism": f"{nthreads} host threads"},
         "cpu_baseline": {"value": value, "unit": "trees/s", "cores": nthreads, "kind": "oracle", "sample": sample},

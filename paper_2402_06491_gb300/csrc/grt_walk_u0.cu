@@ -1,5 +1,5 @@
 // grt_walk_u0.cu -- the FP32 featureless walk with the kind of initial data
-// fixed at compile time, in one launch shape per compilation: the build
+// fixed at compile time, in one launch shape per compilation: build.py
 // compiles this file once per shape the walk offers (4 or 8 warps per block,
 // the whole stack or its top three levels in shared memory), defining
 // GRT_U0_FN (the launch function's name), GRT_U0_WARPS and GRT_U0_SLEV.

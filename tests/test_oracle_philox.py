@@ -1,6 +1,6 @@
 """Pins of the oracle's counter-based generator (Philox4x32-10, Salmon et al. SC'11).
 
-The paper does not name its generator; the build keys every node's draws by
+The paper does not name its generator; both the oracle and the GPU path key every node's draws by
 (point, tree, node label) with Philox4x32-10.  The oracle's implementation is
 pinned against an independent implementation of the same published
 definition (Triton's, run by its CPU interpreter), and by statistics.
