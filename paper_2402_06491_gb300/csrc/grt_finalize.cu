@@ -55,24 +55,47 @@ __device__ __forceinline__ void load4(const double *p, double (&w)[4]) {
 // elimination with partial pivoting; a pivot at or below 1e-14 times the
 // largest entry lowers the type to [L-1/M-1] (L not below 0) and sets
 // PADE_SINGULAR.  |Q(1)| < 1e-8 sets PADE_POLE_NEAR.
+
+// Integer forms of the Pade's comparisons and exponent steps (FP64 instructions are the
+// evaluation's cost on this GPU): |v| compared through its bit pattern, which orders like |v|;
+// ilogb and scalbn by the exponent field for normal numbers (exact), the library routines
+// otherwise.  Every decision and value is the same as with the FP64 forms.
+__device__ __forceinline__ uint64_t pd_abs_bits(double v) {
+  return (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+// |v| as an integer key ordered like |v|; NaN -> 0 (loses every strict comparison, as in FP64)
+__device__ __forceinline__ uint64_t pd_key(double v) {
+  const uint64_t b = pd_abs_bits(v);
+  return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+__device__ __forceinline__ int pd_ilogb(double v) {
+  const int e = (int)(((uint64_t)__double_as_longlong(v) >> 52) & 0x7FF);
+  return (e == 0 || e == 0x7FF) ? ilogb(v) : e - 1023;
+}
+__device__ __forceinline__ double pd_scalbn(double v, int n) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0 || e == 0x7FF || e + n <= 0 || e + n >= 0x7FF) return scalbn(v, n);
+  return __longlong_as_double((long long)(b + ((uint64_t)(int64_t)n << 52)));
+}
 __device__ double pade_value(const double *a, int L, int M, int *status) {
   const int n = L + M;
   // growth rate of the series by the root test on its binary exponents,
   // rounded up to an integer: rho = 2^k, so the rescaling below is exact
   int first = 0;
-  while (first <= n && a[first] == 0.0) ++first;
+  while (first <= n && pd_abs_bits(a[first]) == 0) ++first;
   int k = 0;
   bool any = false;
   for (int j = first + 1; j <= n; ++j) {
-    if (a[j] == 0.0) continue;
-    const int num = ilogb(a[j]) - ilogb(a[first]), den = j - first;
+    if (pd_abs_bits(a[j]) == 0) continue;
+    const int num = pd_ilogb(a[j]) - pd_ilogb(a[first]), den = j - first;
     const int q = num > 0 ? (num + den - 1) / den : -((-num) / den);  // ceil(num / den)
     k = any ? max(k, q) : q;
     any = true;
   }
   const double rho = scalbn(1.0, k);
   double c[kMaxK + 1];
-  for (int i = 0; i <= n; ++i) c[i] = scalbn(a[i], -k * i);
+  for (int i = 0; i <= n; ++i) c[i] = pd_scalbn(a[i], -k * i);
 
   int st = 0;
   int Lc = L, Mc = M;
@@ -80,30 +103,34 @@ __device__ double pade_value(const double *a, int L, int M, int *status) {
   beta[0] = 1.0;
   while (Mc > 0) {
     double T[kMaxK][kMaxK + 1];  // row r: coefficients of beta_1..beta_Mc, then the right side
-    double big = 0.0;
+    uint64_t bigk = 0;
     for (int r = 0; r < Mc; ++r) {
       for (int k = 0; k < Mc; ++k) {
         const int idx = Lc + r - k;  // c_{L+i-j} with i = r+1, j = k+1
         const double v = idx >= 0 ? c[idx] : 0.0;
         T[r][k] = v;
-        big = fmax(big, fabs(v));
+        bigk = max(bigk, pd_key(v));
       }
       T[r][Mc] = -c[Lc + r + 1];
     }
-    bool ok = big > 0.0;
+    bool ok = bigk > 0;
+    const uint64_t tiny = pd_key(1e-14 * __longlong_as_double((long long)bigk));
     for (int k = 0; k < Mc && ok; ++k) {
       int pr = k;
-      double pv = fabs(T[k][k]);
-      for (int r = k + 1; r < Mc; ++r) {
-        const double v = fabs(T[r][k]);
-        if (v > pv) {
-          pv = v;
-          pr = r;
+      const uint64_t b0 = pd_abs_bits(T[k][k]);
+      if (b0 <= 0x7FF0000000000000ull) {  // a NaN pivot candidate keeps its row, as the FP64 scan does
+        uint64_t pvk = b0;
+        for (int r = k + 1; r < Mc; ++r) {
+          const uint64_t vk = pd_key(T[r][k]);
+          if (vk > pvk) {
+            pvk = vk;
+            pr = r;
+          }
         }
-      }
-      if (pv <= 1e-14 * big) {
-        ok = false;
-        break;
+        if (pvk <= tiny) {
+          ok = false;
+          break;
+        }
       }
       if (pr != k) {
         for (int j = k; j <= Mc; ++j) {
@@ -115,7 +142,7 @@ __device__ double pade_value(const double *a, int L, int M, int *status) {
       const double inv = 1.0 / T[k][k];
       for (int r = k + 1; r < Mc; ++r) {
         const double m = T[r][k] * inv;
-        if (m != 0.0)
+        if (pd_abs_bits(m) != 0)
           for (int j = k; j <= Mc; ++j) T[r][j] -= m * T[k][j];
       }
     }
