@@ -152,6 +152,27 @@ def test_per_tree_records(grt, name, pb, x, t, K):
         assert rel_ok[aw > 1e-30].mean() > 0.99, rel_ok.mean()
 
 
+@pytest.mark.parametrize("pb", [workloads.problem_sin_2d(), workloads.problem_pdd_3d(),
+                                workloads.problem_kpp_1d()], ids=["sin_2d fp32", "pdd_3d fp32", "kpp_1d fp64"])
+def test_per_tree_records_at_the_largest_indices(grt, pb):
+    """The last trees a point can have (tree indices up to 2^31 - 1, the top bit of the counter
+    word being the second-call flag) of the last point index (2^32 - 1): same records."""
+    d = pb["dim"]
+    x = [0.3, -0.7, 1.1][:d]
+    first, n, point = (1 << 31) - 300, 300, (1 << 32) - 1
+    ctx = grt.grt_create(pb, 0)
+    g = grt.grt_trees(ctx, x, 0.8, point, first, n, 10, 99)
+    with pytest.raises(grt.GrtError):  # one tree past the counter range
+        grt.grt_trees(ctx, x, 0.8, point, first, n + 1, 10, 99)
+    ctx.close()
+    o = oracle.trees(pb, x, 0.8, point, first, n, 10, 99)
+    assert np.array_equal(g["order"], o["order"]) and np.array_equal(g["nodes"], o["nodes"])
+    assert np.array_equal(g["hash"], o["hash"])
+    aw = np.abs(o["w"])
+    rtol = 1e-12 if pb["precision"] == "fp64" else 3e-5
+    assert np.all(np.abs(g["w"] - o["w"]) <= rtol * aw + (1e-13 if pb["precision"] == "fp64" else 1e-6) * aw.max())
+
+
 def test_unit_profile_leaves_gpu_trees_unchanged(grt):
     # gamma = exp(0) = 1 on every term: the records must equal the constant-coefficient walk bit for bit
     base = dict(dim=2, D=0.5, f_coef=[0.2, -0.5, 1.0, 0.3], u0=("gauss", (0.1, 1.0, 0.8, 0.2, -0.3)), strategy="B",
