@@ -227,7 +227,8 @@ int grt_plan_graph_launch(grt_plan *plan, void *stream);
 void grt_plan_destroy(grt_plan *plan);
 
 /* Cancellation factor kappa_n = SA_n / |S1_n| (sum of |W| over the sum of W of the
- * trees of order n) of every point of the plan's last execution, from its
+ * trees of order n; Sec. 2.4, Eq. simplecase_discrete: a_n is the sample mean of
+ * those weights) of every point of the plan's last execution, from its
  * resident per-chunk sums: a kappa far above 1 says that order's mean is a
  * small difference of large weights (its relative statistical error grows
  * with kappa).  d_kappa: DEVICE [n][K+1]; 0 where no tree has that order, +inf
