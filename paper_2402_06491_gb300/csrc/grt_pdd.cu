@@ -3,9 +3,9 @@
 // values and independent Crank-Nicolson solves of the subdomains.
 //
 // GPU layout:
-//   * spline: a weights kernel (one thread per nodal column: the not-a-knot
-//     system of a unit data vector by elimination, then the cubic at every
-//     target) and an axis-contraction kernel applied once per axis, FP64;
+//   * spline: a weights kernel (one thread per target and nodal column: the
+//     not-a-knot system of a unit data vector by elimination, then the cubic
+//     at that target) and an axis-contraction kernel applied once per axis, FP64;
 //   * local solver: a cluster of two thread blocks per subdomain (each owning
 //     half of the rows, the peer's half read through distributed shared
 //     memory) -- or one block when a half does not fit in shared memory --
@@ -38,10 +38,14 @@ namespace grt {
 // M_2..M_{n-3} (Thomas elimination).  On [x_i, x_{i+1}], A = (x_{i+1} - x)/hn,
 // B = 1 - A: s = A y_i + B y_{i+1} + ((A^3 - A) M_i + (B^3 - B) M_{i+1}) hn^2 / 6.
 // ---------------------------------------------------------------------------
+// One thread per (target t, node j): the thread solves for the M_i of e_j (n is small: the
+// spline's nodes on one axis) and evaluates that one target, so a launch is as long as one
+// O(n) solve rather than a node's whole list of targets.
 __global__ void spline_weights_kernel(int n, double lo, double hn, int m, const double *__restrict__ targets,
                                       double *__restrict__ W) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * m) return;
+  const int j = (int)(e % n), t = (int)(e / n);
   double M[GRT_SPLINE_MAX_NODES], cp[GRT_SPLINE_MAX_NODES];
   const double s6 = 6.0 / (hn * hn);
   auto r_at = [&](int i) -> double {  // 6 (y_{i+1} - 2 y_i + y_{i-1}) / hn^2 for y = e_j
@@ -66,17 +70,22 @@ __global__ void spline_weights_kernel(int n, double lo, double hn, int m, const 
   M[0] = 2.0 * M[1] - M[2];
   M[n - 1] = 2.0 * M[n - 2] - M[n - 3];
   const double hh6 = hn * hn / 6.0;
-  for (int t = 0; t < m; ++t) {
-    const double xt = targets[t];
-    int i = (int)floor((xt - lo) / hn);
-    i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
-    const double A = (lo + (double)(i + 1) * hn - xt) / hn, B = 1.0 - A;
-    double v = 0.0;
-    if (i == j) v += A;
-    if (i + 1 == j) v += B;
-    v += ((A * A * A - A) * M[i] + (B * B * B - B) * M[i + 1]) * hh6;
-    W[(size_t)t * n + j] = v;
-  }
+  const double xt = targets[t];
+  int i = (int)floor((xt - lo) / hn);
+  i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+  const double A = (lo + (double)(i + 1) * hn - xt) / hn, B = 1.0 - A;
+  double v = 0.0;
+  if (i == j) v += A;
+  if (i + 1 == j) v += B;
+  v += ((A * A * A - A) * M[i] + (B * B * B - B) * M[i + 1]) * hh6;
+  W[(size_t)t * n + j] = v;
+}
+
+static void launch_spline_weights(int n, double lo, double hn, int m, const double *targets, double *W,
+                                  cudaStream_t s) {
+  const long long total = (long long)n * m;
+  if (total <= 0) return;
+  spline_weights_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(n, lo, hn, m, targets, W);
 }
 
 // out[o][i][r] = sum_j W[i][j] in[o][j][r]: one axis of the tensor-product spline.
@@ -698,8 +707,7 @@ int grt_spline_grid(grt_ctx *c, int ndim, const int32_t *n_nodes, const double *
     wo[a] = woff;
     to[a] = toff;
     const double hn = (hi[a] - lo[a]) / (n_nodes[a] - 1);
-    grt::spline_weights_kernel<<<(n_nodes[a] + 63) / 64, 64, 0, s>>>(n_nodes[a], lo[a], hn, n_targets[a],
-                                                                       dtg + toff, W + woff);
+    grt::launch_spline_weights(n_nodes[a], lo[a], hn, n_targets[a], dtg + toff, W + woff, s);
     woff += (long long)n_targets[a] * n_nodes[a];
     toff += n_targets[a];
   }
@@ -831,10 +839,10 @@ int grt_pdd_solve_range(grt_ctx *c, const grt_pdd_grid *g, int64_t sub_begin, in
                                                       q.mu[0], d > 1 ? q.mu[1] : q.mu[0], d > 2 ? q.mu[2] : q.mu[0],
                                                       Dt + ioff);
   // weights: time axis (t_nodes + 1 uniform levels over [0, T]) and every space axis
-  grt::spline_weights_kernel<<<1, 256, 0, s>>>(tn, 0.0, g->T / g->t_nodes, g->nsteps, tg, W);
+  grt::launch_spline_weights(tn, 0.0, g->T / g->t_nodes, g->nsteps, tg, W, s);
   for (int a = 0; a < d; ++a)
-    grt::spline_weights_kernel<<<(g->nodes[a] + 63) / 64, 64, 0, s>>>(
-        g->nodes[a], q.lo[a], (g->hi[a] - g->lo[a]) / (g->nodes[a] - 1), q.N[a], tg + toff_ax[a], W + woff_ax[a]);
+    grt::launch_spline_weights(g->nodes[a], q.lo[a], (g->hi[a] - g->lo[a]) / (g->nodes[a] - 1), q.N[a],
+                               tg + toff_ax[a], W + woff_ax[a], s);
   GRT_CUDA(c, cudaGetLastError());
 
   // spline every axis's planes
