@@ -147,14 +147,35 @@ template <> struct Math<double> {
 // its accuracy holds on the argument range:
 //   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ, ~2 ulp)
 //   e^v           = 2^(v log2 e) by ex2.approx, the log2 e folded into the caller's constant
-// ln U uses the accurate library function and sin / cos of 2 pi U an octant
-// reduction on the bits of the Philox word with short Taylor polynomials: the
-// SFU's absolute error (~2^-22) would become a large relative error of -2 ln U
-// for U near 1 and of the normals, which shows up in u0 near its zeros.  The
-// FP64 walk uses the library functions throughout.
+//   -2 ln U       = -2 ln 2 log2 U by lg2.approx for U <= 1/2, where |log2 U| >= 1 turns
+//                   the SFU's small absolute error into a small relative one; for U > 1/2,
+//                   where it would not, 4 atanh(z) with z = V / (2 - V), V = 1 - U (exact):
+//                   -ln(1 - V) = 2 atanh(z), and z <= 1/3 makes the odd series to z^15
+//                   exact to float precision (within 3.3 ulp over all 2^23 values of U)
+// and sin / cos of 2 pi U an octant reduction on the bits of the Philox word
+// with short Taylor polynomials.  The FP64 walk uses the library functions.
 template <typename Real> struct Node;
 template <> struct Node<float> {
-  static __device__ __forceinline__ float neg2ln(float u) { return -2.0f * logf(u); }
+  static __device__ __forceinline__ float neg2ln(float u) {
+    float l2;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(u));
+    const float lo = -1.38629436111989061883f * l2;  // -2 ln 2 log2 U
+    const float v = 1.0f - u;                         // exact for U in (1/2, 1)
+    const float d = 2.0f - v;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    float z = v * r;
+    z = fmaf(r, fmaf(-z, d, v), z);  // one residual correction of v / d
+    const float z2 = z * z;
+    float p = fmaf(z2, 1.0f / 15.0f, 1.0f / 13.0f);
+    p = fmaf(z2, p, 1.0f / 11.0f);
+    p = fmaf(z2, p, 1.0f / 9.0f);
+    p = fmaf(z2, p, 1.0f / 7.0f);
+    p = fmaf(z2, p, 1.0f / 5.0f);
+    p = fmaf(z2, p, 1.0f / 3.0f);
+    const float hi = 4.0f * fmaf(z * z2, p, z);  // 4 atanh z = 4 (z + z^3/3 + ... + z^15/15)
+    return u <= 0.5f ? lo : hi;
+  }
   // sin and cos of 2 pi U(w) from the bits of w: the top three bits pick the
   // octant, the next twenty the offset in it, so no floating-point range
   // reduction is needed.  With o = w >> 29 and rr the 20-bit offset (mirrored
