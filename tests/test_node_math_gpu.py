@@ -4,7 +4,7 @@ value U = ((w >> 9) + 1/2) 2^-23 the uniform map produces (2^23 of them):
   * -2 ln U: the special-function unit's log2 for U <= 1/2 (its absolute error is then a
     relative one, |log2 U| >= 1), the series 4 atanh(z), z = (1 - U) / (1 + U), above.
     Bound: 4 ulp of the float result everywhere.
-  * sin and cos of 2 pi U from the bits of w (octant from the top three bits, Taylor
+  * sin and cos of 2 pi U from the bits of w (octant from the top three bits, near-minimax
     polynomials on [0, pi/4]) and the cosine alone (the third normal in 3-D).  Bound: 2 ulp.
 """
 import os
