@@ -145,7 +145,7 @@ template <> struct Math<double> {
 
 // Node-body arithmetic.  The FP32 walk uses the special-function unit where
 // its accuracy holds on the argument range:
-//   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (MUFU.RSQ, ~2 ulp)
+//   sqrt(v)       = v * rsqrt(v), 0 for v = 0             (rsqrt.approx, ~2 ulp)
 //   e^v           = 2^(v log2 e) by ex2.approx, the log2 e folded into the caller's constant
 //   -2 ln U       = -2 ln 2 log2 U by lg2.approx for U <= 1/2, where |log2 U| >= 1 turns
 //                   the SFU's small absolute error into a small relative one; for U > 1/2,
@@ -216,7 +216,13 @@ template <> struct Node<float> {
     const float b = ((t >> 30) & 1u) ? sp : cp;
     return __uint_as_float(__float_as_uint(b) ^ (t & 0x80000000u));
   }
-  static __device__ __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
+  // v rsqrt(v) by the PTX rsqrt.approx instruction on an argument kept normal (the library
+  // rsqrtf adds a subnormal path the walk never needs); 0 for v = 0
+  static __device__ __forceinline__ float sqrt_pos(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(v, 1e-37f)));
+    return v * r;
+  }
   // 2^v by the PTX ex2.approx.ftz.f32 instruction (v already times log2 e; results
   // below the normal range flush to zero, which no weight of interest reaches)
   static __device__ __forceinline__ float exp_scaled(float v) {

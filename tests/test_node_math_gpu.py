@@ -6,6 +6,8 @@ value U = ((w >> 9) + 1/2) 2^-23 the uniform map produces (2^23 of them):
     Bound: 4 ulp of the float result everywhere.
   * sin and cos of 2 pi U from the bits of w (octant from the top three bits, near-minimax
     polynomials on [0, pi/4]) and the cosine alone (the third normal in 3-D).  Bound: 2 ulp.
+  * the radius sqrt(-2 ln U) as the walk forms it (v rsqrt(v) of the value above).  Bound:
+    4 ulp.
 """
 import os
 import shutil
@@ -27,7 +29,7 @@ __device__ float ulp_err(float f, double ref) {
   const double ulp = (double)nextafterf(fabsf(rf), INFINITY) - (double)fabsf(rf);
   return (float)(fabs((double)f - ref) / ulp);
 }
-// err[j][m]: j = 0 -2 ln U, 1 sin 2 pi U, 2 cos 2 pi U, 3 the cosine alone
+// err[j][m]: j = 0 -2 ln U, 1 sin 2 pi U, 2 cos 2 pi U, 3 the cosine alone, 4 the radius
 __global__ void k(float *err) {
   const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned n = 1u << 23;
@@ -42,15 +44,16 @@ __global__ void k(float *err) {
   err[n + m] = ulp_err(s, rs);
   err[2 * n + m] = ulp_err(c, rc);
   err[3 * n + m] = ulp_err(grt::Node<float>::cos2pi_w(w), rc);
+  err[4 * n + m] = ulp_err(grt::Node<float>::sqrt_pos(grt::Node<float>::neg2ln(u)), sqrt(-2.0 * log((double)u)));
 }
 int main() {
   const unsigned n = 1u << 23;
   float *d;
-  if (cudaMalloc(&d, 4ull * n * sizeof(float)) != cudaSuccess) return 2;
+  if (cudaMalloc(&d, 5ull * n * sizeof(float)) != cudaSuccess) return 2;
   k<<<n / 256, 256>>>(d);
-  float *h = new float[4ull * n];
-  if (cudaMemcpy(h, d, 4ull * n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return 3;
-  for (int j = 0; j < 4; ++j) {
+  float *h = new float[5ull * n];
+  if (cudaMemcpy(h, d, 5ull * n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return 3;
+  for (int j = 0; j < 5; ++j) {
     double mx = 0, sum = 0;
     unsigned at = 0;
     for (unsigned i = 0; i < n; ++i) {
@@ -78,8 +81,9 @@ def test_box_muller_arithmetic_for_every_uniform(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     rows = [line.split() for line in r.stdout.strip().splitlines()]
-    assert len(rows) == 4, r.stdout
-    bounds = [("-2 ln U", 4.0), ("sin 2 pi U", 2.0), ("cos 2 pi U", 2.0), ("cos 2 pi U alone", 2.0)]
+    assert len(rows) == 5, r.stdout
+    bounds = [("-2 ln U", 4.0), ("sin 2 pi U", 2.0), ("cos 2 pi U", 2.0), ("cos 2 pi U alone", 2.0),
+              ("radius", 4.0)]
     for (name, bound), (mx, at, mean) in zip(bounds, rows):
         assert float(mx) <= bound, (name, mx, at)
         assert float(mean) <= 1.0, (name, mean)
