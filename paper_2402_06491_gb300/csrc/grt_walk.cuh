@@ -121,11 +121,36 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
     x[i] = Real(0);
   }
   uint32_t nodes = 0;  // nodes this lane visited
+  // this lane takes tree c_next + rank of the warp's current chunk
+  auto start_tree = [&](uint32_t rank) {
+    tree = c_first + c_next + rank;  // the tree's index in its point's stream
+    point = c_point;
+    pidx = c_pt;
+    rec = c_rec + c_next + rank;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      base[i] = c_base[i];
+      x[i] = Real(0);
+    }
+    tau = c_t;
+    W = Real(1);
+    id_lo = 0;
+    id_hi = 0;
+    Ne = 0;
+    depth = 0;
+    active = true;
+  };
 
   for (;;) {
     // ---- hand unstarted trees to idle lanes ---------------------------------
     unsigned idle = __ballot_sync(kFull, !active);
-    if (idle != 0u) {
+    const uint32_t want0 = (uint32_t)__popc(idle);
+    // common case: the current chunk has a tree for every idle lane (one pass, no chunk fetch);
+    // otherwise the general loop below fetches chunks until every idle lane has a tree
+    if (idle != 0u && c_end - c_next >= want0) {
+      if (!active) start_tree((uint32_t)__popc(idle & lt_mask));
+      c_next += want0;
+    } else if (idle != 0u) {
       while (idle != 0u && !exhausted) {
         if (c_next >= c_end) {
           uint32_t item = 0;
@@ -152,24 +177,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
         const uint32_t avail = c_end - c_next;
         const uint32_t want = (uint32_t)__popc(idle);
         const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
-        if (((idle >> lane) & 1u) && rank < avail) {
-          tree = c_first + c_next + rank;  // the tree's index in its point's stream
-          point = c_point;
-          pidx = c_pt;
-          rec = c_rec + c_next + rank;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            base[i] = c_base[i];
-            x[i] = Real(0);
-          }
-          tau = c_t;
-          W = Real(1);
-          id_lo = 0;
-          id_hi = 0;
-          Ne = 0;
-          depth = 0;
-          active = true;
-        }
+        if (((idle >> lane) & 1u) && rank < avail) start_tree(rank);
         if (avail >= want) {  // every idle lane got a tree
           c_next += want;
           idle = 0u;
