@@ -751,8 +751,9 @@ def gpu_arm(args) -> int:
             "traffic": walk_prof[0] if not args.trees else None,
             "issue_active_ncu": walk_prof[1]["issue_active"] if walk_prof[1] else None,
             "ncu": walk_prof[1],
-            "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case; "
-                          "profiles/walk_kernel_sin2d.md): the hardware's SM issue-slot utilisation, "
+            "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case, shape "
+                          "{4 warps, whole stack in shared memory}; profiles/walk_kernel_sin2d.md): the "
+                          "hardware's SM issue-slot utilisation, "
                           "beside the stricter algorithmic fraction `frac`; `ncu` adds the ALU and FMA "
                           "pipe utilisation and the warp-divergence efficiency (active lanes / 32)",
             "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md); "
