@@ -689,7 +689,9 @@ def gpu_arm(args) -> int:
                 "3e-5 (tested): worst case 3e-5 kappa_n |a_n| per coefficient (kappa_n = SA_n/|S1_n|, "
                 "grt_plan_kappa), and independent per-tree errors 3e-5 sqrt(SE_n^2 + a_n^2/N)"}
 
-    # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result
+    # end to end through the public host-buffer call: H2D of the step's inputs, D2H of its result;
+    # the one-shot solve takes the plan's launch shape
+    grt.grt_set_solve_config(ctx, grt.grt_plan_get_config(plan))
     e2e_steps = 0 if args.no_e2e else max(args.steps, 1)
     xh = torch.from_numpy(wl["x"]).pin_memory().numpy()
     th = torch.from_numpy(wl["t"]).pin_memory().numpy()

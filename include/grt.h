@@ -208,6 +208,12 @@ int grt_plan_launches(const grt_plan *plan);
 int grt_plan_set_config(grt_plan *plan, const int32_t *cfg);
 int grt_plan_get_config(const grt_plan *plan, int32_t *cfg);
 
+/* The same launch shape for the context's one-shot grt_solve (for instance the
+ * shape grt_plan_autotune found for a plan of that workload).  Results do not
+ * change.  GRT_EINVAL for a shape outside the list above.  grt_solve_noalloc and
+ * the server keep the default shape. */
+int grt_set_solve_config(grt_ctx *ctx, const int32_t *cfg);
+
 /* Autotuner (batching of uneven budgets into one launch): runs the plan on the
  * given device buffers once per candidate shape (a warm run plus two timed runs,
  * CUDA events on `stream`), keeps the fastest walk, and returns it in cfg_out

@@ -97,6 +97,7 @@ def _load():
         "grt_plan_timing": ([_vp, _P(ctypes.c_float), _P(ctypes.c_float)], i32),
         "grt_plan_launches": ([_vp], i32),
         "grt_plan_set_config": ([_vp, i32p], i32),
+        "grt_set_solve_config": ([_vp, i32p], i32),
         "grt_plan_get_config": ([_vp, i32p], i32),
         "grt_plan_autotune": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp, _vp, i32p], i32),
         "grt_plan_graph_capture": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp], i32),
@@ -344,6 +345,12 @@ def grt_plan_set_config(plan: Plan, cfg) -> None:
     """Walk launch shape [warps, smem stack levels, blocks per SM, trees per queue chunk]."""
     c = np.ascontiguousarray(cfg, dtype=np.int32)
     _check(_load().grt_plan_set_config(plan.handle, _ptr(c, ctypes.c_int32)), plan.ctx.handle)
+
+
+def grt_set_solve_config(ctx: Context, cfg) -> None:
+    """Launch shape [warps, smem_levels, blocks_per_sm, tile] of the context's grt_solve walks."""
+    c = np.ascontiguousarray(np.asarray(cfg, np.int32).reshape(4))
+    _check(_load().grt_set_solve_config(ctx.handle, _ptr(c, ctypes.c_int32)), ctx.handle)
 
 
 def grt_plan_get_config(plan: Plan) -> list:
@@ -621,7 +628,7 @@ def grt_spline_grid(ctx: Context, n_nodes, lo, hi, targets, values, out, batch: 
 
 EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
-            "grt_plan_set_config", "grt_plan_get_config", "grt_plan_autotune", "grt_plan_graph_capture",
+            "grt_plan_set_config", "grt_plan_get_config", "grt_set_solve_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
             "grt_pade", "grt_pade_error", "grt_plan_kappa", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",

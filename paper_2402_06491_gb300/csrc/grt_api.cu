@@ -483,6 +483,11 @@ int grt_solve(grt_ctx *c, int64_t n, const double *x, const double *t, const uin
     if (!c->solve_plan) return c->set_error(GRT_ENOMEM, "out of host memory");
     c->solve_plan->ctx = c;
   }
+  if (c->solve_plan->cfg.tile != c->solve_cfg.tile) {  // other queue chunks: lay the solve out again
+    c->solve_plan->n = -1;
+    c->solve_plan->host_ntrees.clear();
+  }
+  c->solve_plan->cfg = c->solve_cfg;
   int rc = plan_configure(c->solve_plan, n, ntrees, K, L, M);
   if (rc != GRT_OK) return rc;
   GRT_CUDA(c, c->dx.ensure((size_t)n * dim * sizeof(double)));
@@ -574,6 +579,18 @@ int grt_plan_timing(grt_plan *p, float *walk_ms, float *finalize_ms) {
 }
 
 int grt_plan_launches(const grt_plan *p) { return p ? p->launches : 0; }
+
+int grt_set_solve_config(grt_ctx *c, const int32_t *cfg) {
+  if (!c || !cfg) return GRT_EINVAL;
+  if ((cfg[0] != 4 && cfg[0] != 8) || (cfg[1] != 0 && cfg[1] != 3) || cfg[2] < 0 || cfg[3] < 32 ||
+      cfg[3] > (1 << 20) || (cfg[3] & 31))
+    return c->set_error(GRT_EINVAL, "config: warps 4|8, smem_levels 0|3, blocks_per_sm >= 0, tile a multiple of 32");
+  c->solve_cfg.warps = cfg[0];
+  c->solve_cfg.smem_levels = cfg[1];
+  c->solve_cfg.blocks_per_sm = cfg[2];
+  c->solve_cfg.tile = (uint32_t)cfg[3];
+  return GRT_OK;
+}
 
 int grt_plan_set_config(grt_plan *p, const int32_t *cfg) {
   if (!p || !cfg) return GRT_EINVAL;

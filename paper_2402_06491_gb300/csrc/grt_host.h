@@ -9,6 +9,7 @@
 
 #include "grt.h"
 #include "grt_device.cuh"
+#include "grt_launch.h"
 
 namespace grt {
 
@@ -50,6 +51,7 @@ struct grt_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   grt_plan *solve_plan = nullptr;
+  grt::WalkConfig solve_cfg{};  // launch shape of grt_solve's walk (grt_set_solve_config)
   grt::DevBuf dx, dt, du, dcoef, dse, dstatus;
   grt::DevBuf pdd_scratch;  // spline weights, staging, plane data and subdomain vectors of the PDD stages
   int set_error(int code, const std::string &msg) {

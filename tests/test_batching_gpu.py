@@ -137,3 +137,20 @@ def test_every_kind_of_initial_data_in_every_shape(grt, name, dim, strategy, u0,
         from test_parity_gpu import _assert_fp32_parity
         ctol = 1.5e-4 if u0[0] in ("tanh_prod", "cos_prod", "quadratic") else 3e-5
         _assert_fp32_parity(dict(u=outs[0][0], coef=outs[0][1], status=outs[0][2]), o, ntrees, ctol=ctol, L=L, M=M)
+
+
+def test_solve_config_keeps_the_results(grt):
+    """grt_set_solve_config: grt_solve in another launch shape gives the same bits; bad shapes fail."""
+    wl = workloads.subsample(workloads.workload_sin_2d(), 40, ntrees=6000)
+    ctx = grt.grt_create(wl["problem"], 0)
+    args = (wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], 9)
+    ref = grt.grt_solve(ctx, *args)
+    for shape in ([8, 3, 0, 512], [4, 3, 2, 2048], [4, 0, 0, 64]):
+        grt.grt_set_solve_config(ctx, shape)
+        g = grt.grt_solve(ctx, *args)
+        assert np.array_equal(g["coef"], ref["coef"]) and np.array_equal(g["status"], ref["status"])
+        assert np.array_equal(g["u"], ref["u"], equal_nan=True)
+    for bad in ([6, 0, 0, 512], [4, 2, 0, 512], [4, 0, 0, 100]):
+        with pytest.raises(grt.GrtError):
+            grt.grt_set_solve_config(ctx, bad)
+    ctx.close()
