@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
       id_hi = __funnelshift_l(id_lo, id_hi, 4);
       id_lo = (id_lo << 4) | 1u;
     }
-    if (up) {
+    if (up) {  // the next child of the frame on top; a frame whose last child this is is popped
+      // (its digit is still advanced: the slot is free, and a push overwrites all of it)
       const int lvl = depth - 1;
       uint32_t nk, clo;
       if (SLEV == 0 || lvl < lv) {
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
             clo = __float_as_uint(a.w);
             id_hi = b.x;
             nk = b.y;
-            if ((nk & 0xFFu) != (nk >> 8)) reinterpret_cast<uint32_t *>(fr_b)[2 * at + 1] = nk + 1u;
+            reinterpret_cast<uint32_t *>(fr_b)[2 * at + 1] = nk + 1u;
           } else {
             const uint4 b = reinterpret_cast<const uint4 *>(fr_b)[at];
             x[0] = (Real)a.x;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
             clo = b.x;
             id_hi = b.y;
             nk = b.z;
-            if ((nk & 0xFFu) != (nk >> 8)) reinterpret_cast<uint32_t *>(fr_b)[4 * at + 2] = nk + 1u;
+            reinterpret_cast<uint32_t *>(fr_b)[4 * at + 2] = nk + 1u;
           }
         } else {
 #pragma unroll
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
           nk = stk_nk[at];
           clo = stk_lo[at];
           id_hi = stk_hi[at];
-          if ((nk & 0xFFu) != (nk >> 8)) stk_nk[at] = nk + 1u;
+          stk_nk[at] = nk + 1u;
         }
       } else {
         const int at = lvl - lv;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
         nk = lnk[at];
         clo = llo[at];
         id_hi = lhi[at];
-        if ((nk & 0xFFu) != (nk >> 8)) lnk[at] = nk + 1u;
+        lnk[at] = nk + 1u;
       }
       const uint32_t nd = nk & 0xFFu;
       id_lo = clo | nd;
