@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -53,6 +54,11 @@ struct grt_plan {
   bool timing = false, timed_last = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   grt::WalkConfig cfg{};             // launch shape of the walk (autotuned or set)
+  // walk launches: points [group_pt[g], group_pt[g+1]), whose records span fewer than 2^32 slots
+  // (one group unless the plan holds that many records)
+  std::vector<int64_t> group_pt;
+  std::vector<uint32_t> group_item;        // first queue item of each group (and the end)
+  std::vector<unsigned long long> group_rec;  // first record slot of each group
   cudaGraph_t graph = nullptr;       // a captured execution (grt_plan_graph_capture)
   cudaGraphExec_t graph_exec = nullptr;
   void release() {
@@ -328,6 +334,27 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   GRT_CUDA(c, cudaMemcpy(p->chunk_prefix.ptr, cprefix.data(), cprefix.size() * sizeof(uint32_t),
                          cudaMemcpyHostToDevice));
   GRT_CUDA(c, cudaMemset(p->work.ptr, 0, p->work_bytes));
+  // walk launch groups: consecutive points whose record slots span fewer than `window`
+  unsigned long long window = 0xFFFFFFFFull;
+  if (const char *ev = std::getenv("GRT_MAX_RECORDS_PER_LAUNCH")) {  // testing aid: smaller windows
+    const unsigned long long v = std::strtoull(ev, nullptr, 10);
+    if (v >= 4096 && v < window) window = v;
+  }
+  p->group_pt.assign(1, 0);
+  p->group_item.assign(1, 0);
+  p->group_rec.assign(1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const unsigned long long seg_end = tprefix[(size_t)i + 1];
+    if (seg_end - p->group_rec.back() > window && i > p->group_pt.back()) {
+      p->group_pt.push_back(i);
+      p->group_item.push_back(prefix[(size_t)i]);
+      p->group_rec.push_back(tprefix[(size_t)i]);
+    }
+    if (seg_end - p->group_rec.back() > 0xFFFFFFFFull)
+      return c->set_error(GRT_EINVAL, "one point's records span 2^32 slots");
+  }
+  p->group_pt.push_back(n);
+  p->group_item.push_back((uint32_t)items);
   p->total_chunks = (uint32_t)chunks;
   p->n = n;
   p->K = K;
@@ -336,7 +363,7 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   p->total_items = (uint32_t)items;
   p->total_trees = trees;
   p->host_ntrees.assign(ntrees, ntrees + n);
-  p->launches = items > 0 ? 2 : 1;
+  p->launches = items > 0 ? 1 + (int)(p->group_pt.size() - 1) : 1;
   return GRT_OK;
 }
 
@@ -367,8 +394,17 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   const bool fp64 = c->pb.precision == GRT_FP64;
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[0], stream));
   GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, p->work_bytes, stream));
-  if (p->total_items > 0)
+  for (size_t g = 0; g + 1 < p->group_pt.size() && p->total_items > 0; ++g) {
+    if (p->group_item[g + 1] == p->group_item[g]) continue;  // no trees in this group
+    if (g > 0) GRT_CUDA(c, cudaMemsetAsync(p->work.ptr, 0, sizeof(uint32_t), stream));  // queue head
+    w.n = (int)p->group_pt[g + 1];  // the point search covers points below the group's end
+    w.item_base = p->group_item[g];
+    w.total_items = p->group_item[g + 1];
+    w.rec_base = p->group_rec[g];
+    w.rec_w = static_cast<unsigned char *>(p->rec_w.ptr) + (size_t)p->group_rec[g] * acc_size(c);
+    w.rec_o = p->rec_o.as<uint8_t>() + p->group_rec[g];
     GRT_CUDA(c, grt::launch_walk(fp64, c->pb.dim, c->pb.strategy, w, p->cfg, c->num_sms, stream));
+  }
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[1], stream));
   grt::FinalizeParams f{};
   f.rec_w = p->rec_w.ptr;

@@ -70,7 +70,10 @@ struct WalkParams {
   const uint32_t *point_id;    // [n] random-stream point index of each point, or null (point_base + p)
   int n;
   uint32_t tile;             // trees per queue chunk
-  uint32_t total_items;      // queue chunks
+  uint32_t total_items;      // queue chunks: this launch takes items item_base .. total_items - 1
+  uint32_t item_base;
+  unsigned long long rec_base;  // record slot of rec_w[0] / rec_o[0] (the pointers are offset by it):
+                                // a launch's records span fewer than 2^32 slots
   void *rec_w;               // [total trees] tree weights (float or double)
   uint8_t *rec_o;            // [total trees] tree orders (K+1 = pruned)
   unsigned long long *stats; // [0] nodes visited (added by the walk), [1] splits, [2] pruned trees (the binning)

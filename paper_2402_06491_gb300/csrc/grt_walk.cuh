@@ -19,7 +19,9 @@
 // and no lane idles at chunk boundaries.
 //
 // Each finished tree writes its record (order Ne or K+1 if pruned, weight W)
-// to its slot in HBM: rec_o / rec_w [tree_prefix[p] + tree - tree_first[p]].
+// to its slot in HBM: rec_o / rec_w [tree_prefix[p] + tree - tree_first[p]],
+// held as a 32-bit offset from the launch's rec_base (the host splits a plan
+// whose records span 2^32 slots or more into several launches).
 // (An incremental solve walks trees tree_first[p] .. tree_first[p] + ntrees[p] - 1
 // of point p; a one-shot solve has tree_first = 0.)  The series
 // binning of Sec. 2.4 is done from these records by the finalize kernel in a
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
 
   // warp-uniform: the chunk trees are handed out from
   uint32_t c_next = 0, c_end = 0, c_point = 0, c_first = 0, c_pt = 0;
-  uint64_t c_rec = 0;
+  uint32_t c_rec = 0;  // record slot of the chunk's first tree, relative to p.rec_base
   Real c_t = Real(0), c_base[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) c_base[i] = Real(0);
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
   // lane: its tree and the tree's point
   bool active = false;
   uint32_t tree = 0, point = 0, pidx = 0;
-  uint64_t rec = 0;
+  uint32_t rec = 0;    // the tree's record slot, relative to p.rec_base
   Real base[DIM];
   // lane: the current node (position, remaining time, label) and the running tree
   Real x[DIM], tau = Real(0), W = Real(1);
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
       while (idle != 0u && !exhausted) {
         if (c_next >= c_end) {
           uint32_t item = 0;
-          if (lane == 0) item = atomicAdd(p.counter, 1u);
+          if (lane == 0) item = atomicAdd(p.counter, 1u) + p.item_base;
           item = __shfl_sync(kFull, item, 0);
           if (item >= p.total_items) {
             exhausted = true;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(WARPS * 32) walk_kernel(const WalkParams p) {
           c_end = min(c_next + p.tile, N);
           c_point = p.point_id ? __ldg(p.point_id + pt) : p.point_base + (uint32_t)pt;
           c_first = p.tree_first ? __ldg(p.tree_first + pt) : 0u;
-          c_rec = __ldg(p.tree_prefix + pt);
+          c_rec = (uint32_t)(__ldg(p.tree_prefix + pt) - p.rec_base);
           c_t = (Real)__ldg(p.t + pt);
           c_pt = (uint32_t)pt;
           double xp[DIM];
@@ -402,7 +404,7 @@ inline cudaError_t launch_walk_t(const WalkParams &p, const WalkConfig &cfg, int
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
   long grid = (long)per_sm * num_sms;
-  const long need = ((long)p.total_items + WARPS - 1) / WARPS;
+  const long need = ((long)(p.total_items - p.item_base) + WARPS - 1) / WARPS;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, WARPS * 32, smem, stream>>>(p);

@@ -154,3 +154,32 @@ def test_solve_config_keeps_the_results(grt):
         with pytest.raises(grt.GrtError):
             grt.grt_set_solve_config(ctx, bad)
     ctx.close()
+
+
+def test_walk_split_into_record_windows_gives_the_same_bits(grt, monkeypatch):
+    """A plan whose records span more slots than one launch addresses (2^32) is walked as several
+    launches over consecutive point ranges.  Forced here with a small window: same bits, same node
+    counts, one walk launch per window."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.subsample(workloads.workload_uneven_2d(), 48, ntrees=None)
+    nt = np.asarray(wl["ntrees"], np.uint64).copy()
+    nt[3] = 0
+    _, b = _device_case(grt, wl)
+    ctx = grt.grt_create(wl["problem"], 0)
+    outs = []
+    for window in (None, "20000"):
+        if window is None:
+            monkeypatch.delenv("GRT_MAX_RECORDS_PER_LAUNCH", raising=False)
+        else:
+            monkeypatch.setenv("GRT_MAX_RECORDS_PER_LAUNCH", window)
+        plan = grt.grt_plan_create(ctx, nt, wl["K"], wl["L"], wl["M"])
+        grt.grt_plan_execute(plan, b["x"], b["t"], 5, 0, b["u"], b["coef"], None, b["status"])
+        torch.cuda.synchronize()
+        outs.append((b["u"].cpu().numpy().copy(), b["coef"].cpu().numpy().copy(), b["status"].cpu().numpy().copy(),
+                     grt.grt_plan_counters(plan), grt.grt_plan_launches(plan)))
+        plan.close()
+    ctx.close()
+    (u0, c0, s0, n0, l0), (u1, c1, s1, n1, l1) = outs
+    assert l0 == 2 and l1 > 3, (l0, l1)
+    assert np.array_equal(c0, c1) and np.array_equal(s0, s1) and np.array_equal(u0, u1, equal_nan=True)
+    assert n0 == n1
