@@ -171,7 +171,10 @@ int grt_solve(grt_ctx *ctx, int64_t n, const double *x, const double *t, const u
  * and launch many solves of the same shape (e.g. under a CUDA graph).
  * grt_plan_create fixes n, the per-point tree budgets (HOST array, copied) and
  * K, L, M, lays out the (point, tree-tile) work items and allocates every
- * device buffer the solve needs; grt_plan_execute then allocates nothing. */
+ * device buffer the solve needs; grt_plan_execute then allocates nothing.  A
+ * plan whose tree records span 2^32 slots or more (about 4.3e9 trees) is
+ * walked as several launches over consecutive point ranges (the results are
+ * the same; grt_plan_launches counts them). */
 int grt_plan_create(grt_ctx *ctx, int64_t n, const uint64_t *ntrees, int K, int L, int M, grt_plan **out);
 
 /* Enqueue one solve on `stream` (a cudaStream_t; NULL = legacy default stream).
