@@ -72,7 +72,8 @@ __device__ __forceinline__ int find_point(const uint32_t *__restrict__ prefix, i
 
 // __launch_bounds__(threads, 1): without the minimum-blocks hint ptxas aims at more resident
 // blocks and spills some shapes at 40 registers; with it the walk keeps its state in registers
-// (48-61), which is worth more than the extra resident warps (measured in every workload)
+// (48 for the 2-D FP32 kernels, up to 132 for the FP64 ones with features), which is worth more
+// than the extra resident warps (measured in every workload)
 template <typename Real, int DIM, int STRAT, int WARPS, int SLEV, int FEAT = 0, int U0 = -1>
 __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
