@@ -11,7 +11,9 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grt|reference]
 Under torchrun (N > 1) every rank solves its own batch of 512 point solves
 (point streams keyed by rank * 512 + i): weak scaling, no collective on the
 data path; the timed region is bracketed by barriers and the max over ranks
-is taken.  Rank 0 prints one JSON line.
+is taken.  Rank 0 prints one compact JSON line (the last line of stdout); the
+per-result error list, the other workloads' and the serving trace's full
+figures go to a side JSON file (--details, default bench_details.json).
 """
 from __future__ import annotations
 
@@ -36,7 +38,6 @@ import workloads  # noqa: E402
 METRIC = "trees/s, points/s at 1e-5 rel vs oracle; p50/p99 served latency vs plain path"
 WORKLOAD = "sin_2d"
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT_GB300 = 152
 ISSUE_PER_SM_PER_CLK = 4 * 32   # 4 schedulers x 1 warp-instruction x 32 threads
 FP32_WEIGHT_RTOL = 3e-5        # per-tree FP32 weight vs its FP64 value (the per-tree parity bound)
 
@@ -226,8 +227,7 @@ def cpu_baseline(wl: dict, target_s: float, gpu=None) -> dict:
         reps += 1
     n = wl["x"].shape[0]
     out = {"value": trees * reps / total, "unit": "trees/s", "cores": nthreads, "kind": "oracle",
-           "sample": f"first {npts} of {n} point solves of {WORKLOAD} (all 1e5 trees each) x {reps} pass(es), "
-                     f"{total:.1f} s wall on {nthreads} threads"}
+           "sample": f"{npts} of {n} {WORKLOAD} points, all trees, x {reps}, {total:.1f} s"}
     if gpu is not None:
         gu, gc = gpu
         du = np.abs(gu[:npts] - r["u"])
@@ -394,7 +394,7 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
     nsub = int(np.prod(g["sub"]))
     flops = pdd_flops(g)
     fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (not a tensor path)
-    sms = 152
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # blocks per subdomain: a cluster pair when half of the subdomain's four vectors fits in 200 KB
     m = [c - 1 for c in g["cells"]]
     half = 4 * ((m[0] + 1) // 2) * int(np.prod(m[1:])) * 8
@@ -406,8 +406,8 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
                              "frac_of_used_sms": flops / (pd / 1e3) / 1e12
                              / (fp64_peak * min(per_sub * nsub, sms) / sms),
                              "blocks_per_subdomain": per_sub,
-                             "peak_basis": "nominal GB300 FP64 rate (no measured FP64 peak is available); "
-                                           "the subdomain blocks run on min(blocks, 152) SMs"},
+                             "peak_basis": f"nominal GB300 FP64 rate (no measured FP64 peak is available); "
+                                           f"the subdomain blocks run on min(blocks, {sms}) SMs"},
             "subdomain_unknowns": int(np.prod([c - 1 for c in g["cells"]])), "cn_steps": g["nsteps"],
             "point_solve_ms": mc, "pdd_stage_ms": pd, "total_ms": mc + pd, "steps": steps,
             "finite_output": finite,
@@ -732,46 +732,49 @@ def gpu_arm(args) -> int:
     achieved = inst / (walk_avg_ms / 1e3) / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT_GB300 * ISSUE_PER_SM_PER_CLK * sm_max * 1e6 / 1e12
+    n_sms = int(props.multi_processor_count)
+    peak = n_sms * ISSUE_PER_SM_PER_CLK * sm_max * 1e6 / 1e12
     walk_prof = _walk_profile()
+    ncu_figs = walk_prof[1] or {}
     line = {
         "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "points_per_s": points_per_s,
         "config": {
-            "workload": "sin_2d: 2-D u_t = 0.5 Lap u + sin u (degree-9 Taylor, p_k ~ |b_k|, Strategy B), "
-                        "u0 = 1.2 exp(-|x|^2/2), 16x16 grid on [-3,3]^2 x t in {0.25, 1}, 1e5 trees/point, "
-                        "K = 10, FP64 Pade [5/5], FP32 walk",
+            "workload": "sin_2d: 2-D u_t = 0.5 Lap u + sin u (degree-9 Taylor), u0 = 1.2 exp(-|x|^2/2), "
+                        "16x16 grid x t in {0.25, 1}, FP32 walk, FP64 Pade",
             "points": n, "trees_per_point": int(wl["ntrees"][0]), "K": K, "L": L, "M": M,
             "q": round(wl["problem"]["q"], 6), "seed": wl["seed"],
-            "l2": "flushed between steps (256 MiB device write, outside the timed events)",
-            "parallelism": f"{world} GPU(s), points sharded per rank (weak), no data-path collective",
+            "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"{world} GPU(s), points sharded (weak), no collective",
         },
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
             "traffic": walk_prof[0] if not args.trees else None,
-            "issue_active_ncu": walk_prof[1]["issue_active"] if walk_prof[1] else None,
-            "ncu": walk_prof[1],
-            "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case, shape "
-                          "{4 warps, whole stack in shared memory}; profiles/walk_kernel_sin2d.md): the "
-                          "hardware's SM issue-slot utilisation, "
-                          "beside the stricter algorithmic fraction `frac`; `ncu` adds the ALU and FMA "
-                          "pipe utilisation and the warp-divergence efficiency (active lanes / 32)",
-            "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md); "
-                            "algorithmic bytes are the 5 B/tree records = 256 MB written",
-            "kernel": "walk_kernel<float,2,B> (persistent tree walk)",
+            "issue_active_ncu": ncu_figs.get("issue_active"),
+            "lane_efficiency_ncu": ncu_figs.get("lane_efficiency"),
+            "walk_ms": walk_avg_ms, "finalize_ms": float(np.mean(fin_ms)), "graph_ms_per_step": graph_ms,
+            "peak_basis": f"{n_sms} SMs x 128 thread-inst/clk x {sm_max:.0f} MHz; achieved = algorithmic "
+                          f"inst / walk event time",
+        },
+        "e2e": ({"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
+                 "d2h_bytes_per_step": d2h, "matches_device_run": same} if e2e_steps else None),
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+    }
+    # everything else goes to the side file (the headline line stays short enough for log tails)
+    details = {
+        "roofline": {
+            "ncu": walk_prof[1], "walk_config": dict(zip(["warps", "smem_levels", "blocks_per_sm", "tile"], walk_cfg)),
             "work": f"{inst:.4g} algorithmic thread-instructions per launch = {model['node']}/node x {nodes} nodes"
                     f" + {model['leaf']}/leaf x {nodes - splits} + {model['split']}/split x {splits}"
                     f" + {model['tree']}/tree x {int(trees_per_step)}",
-            "walk_ms": walk_avg_ms, "finalize_ms": float(np.mean(fin_ms)),
-            "walk_config": dict(zip(["warps", "smem_levels", "blocks_per_sm", "tile"], walk_cfg)),
-            "graph_ms_per_step": graph_ms,
-            "peak_basis": f"{SM_COUNT_GB300} SMs x 4 issue slots/clk x 32 threads x {sm_max:.0f} MHz (max SM clock)",
+            "issue_note": "smsp__issue_active of the walk kernel (ncu --set full, small case; "
+                          "profiles/walk_kernel_sin2d.md): the hardware's SM issue-slot utilisation, beside the "
+                          "stricter algorithmic fraction `frac`",
+            "traffic_note": "ncu dram__bytes_read+write of one full-size walk launch (profiles/walk_kernel_sin2d.md)",
         },
-        "e2e": ({"value": world * trees_per_step * e2e_steps / e2e_s, "unit": "trees/s", "h2d_bytes_per_step": h2d,
-                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "matches_device_run": same} if e2e_steps else None),
-        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "work_counters": {"nodes": nodes, "splits": splits, "pruned_trees": pruned, "trees": int(trees_per_step)},
         "statistical_error": stat_err,
@@ -781,7 +784,7 @@ def gpu_arm(args) -> int:
     # the single-GPU lines (other workloads, serving, CPU baseline) are measured at N = 1 only: at N > 1
     # the run is about the sharded main workload, and the other GPUs would idle meanwhile
     if not args.no_workloads and world == 1:
-        line["workloads"] = {
+        wls = {
             "uneven_2d": dict(workload_bench(grt, gpu, "uneven_2d", 5), description=(
                 "2-D u_t = Lap u + u^2, u0 = 1.5 + 0.5 cos x cos y, 4096 points on 64 interface segments of the 8x8 "
                 "split of [0,8]^2, t ~ U[0.1, 2], budgets log-uniform in [1e3, 1e6] (5.9e8 trees), K = 16, [8/8]")),
@@ -797,16 +800,87 @@ def gpu_arm(args) -> int:
                 "Example 5: 2-D u_t = Lap u - e^{-x^2}/(t + 0.1) u^2 (variable coefficient), u0 = e^{-x^2/4}/sqrt(4 pi), "
                 "t = 0.5, 16x16 grid in [-3,3]^2, 1e5 trees per point, binary trees q = 2/3, K = 8, [4/4]")),
         }
+        details["workloads"] = wls
+        line["workloads_trees_per_s"] = {k: float(f"{v['trees_per_s']:.4g}") for k, v in wls.items()
+                                         if "trees_per_s" in v}
+        pp = wls["pdd_3d_pipeline"]
+        line["pdd_3d_pipeline_ms"] = {"point_solves": round(pp["point_solve_ms"], 3),
+                                      "pdd_stage": round(pp["pdd_stage_ms"], 3)}
     if not args.no_serving and world == 1:
-        line["serving"] = serving_bench(grt, gpu, value / world, args.serving_requests, args.plain_requests,
-                                        float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
+        srv = serving_bench(grt, gpu, value / world, args.serving_requests, args.plain_requests,
+                            float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
+        details["serving"] = srv
+        line["serving"] = serving_summary(srv)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")),
-                                            gpu=(u_host, coef.cpu().numpy()) if point_base == 0 else None)
-    print(json.dumps(line))
+        cb = cpu_baseline(wl, float(os.environ.get("GRT_CPU_BASELINE_S", "10")),
+                          gpu=(u_host, coef.cpu().numpy()) if point_base == 0 else None)
+        details["cpu_baseline"] = cb
+        short = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        ev = cb.get("error_vs_oracle")
+        if ev is not None:
+            short["error_vs_oracle"] = {k: ev[k] for k in ("points", "max_rel", "median_rel", "within_bar")}
+        line["cpu_baseline"] = short
+    if args.details:
+        try:
+            with open(args.details, "w") as fh:
+                json.dump(dict(line=line, **details), fh, indent=1)
+            line["details"] = args.details
+        except OSError as exc:
+            print(f"bench: could not write {args.details}: {exc}", file=sys.stderr)
+    print(headline_json(line))
+    sys.stdout.flush()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def serving_summary(srv: dict) -> dict:
+    """The serving figures the headline metric names: p50/p99 latency and points/s of the batched
+    server against the plain one-launch-per-point FP64 path, on the same requests."""
+    out = {k: srv.get(k) for k in ("requests", "p50_ms", "p99_ms", "points_per_s", "trees_per_s")}
+    pl = srv.get("plain") or {}
+    out["plain"] = {k: pl.get(k) for k in ("requests", "p50_ms", "p99_ms", "points_per_s",
+                                           "batched_p50_ms_same_requests", "batched_p99_ms_same_requests")}
+    for key in ("shared_launch_steps", "at_configured_rate"):
+        if key in srv:
+            v = srv[key]
+            out[key] = {k: v.get(k) for k in ("p50_ms", "p99_ms", "points_per_s")} if isinstance(v, dict) else v
+    return out
+
+
+HEADLINE_MAX_BYTES = 2400
+# optional keys dropped, in this order, should the headline line outgrow HEADLINE_MAX_BYTES (all of them
+# stay in the side file)
+HEADLINE_OPTIONAL = (("serving", "at_configured_rate"), ("pdd_3d_pipeline_ms",), ("workloads_trees_per_s",),
+                     ("roofline", "graph_ms_per_step"), ("serving",))
+
+
+def headline_json(line: dict) -> str:
+    """The one-line JSON record: floats to 5 significant digits, optional keys dropped while it is
+    longer than HEADLINE_MAX_BYTES."""
+    out = _compact(line)
+    text = json.dumps(out, separators=(",", ":"))
+    for path in HEADLINE_OPTIONAL:
+        if len(text) <= HEADLINE_MAX_BYTES:
+            break
+        d = out
+        for key in path[:-1]:
+            d = d.get(key, {}) if isinstance(d, dict) else {}
+        if isinstance(d, dict) and path[-1] in d:
+            del d[path[-1]]
+            text = json.dumps(out, separators=(",", ":"))
+    return text
+
+
+def _compact(obj, digits: int = 5):
+    """Floats to `digits` significant digits (the headline line is read from a log tail)."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{digits}g}") if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: _compact(v, digits) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_compact(v, digits) for v in obj]
+    return obj
 
 
 def main() -> int:
@@ -824,6 +898,8 @@ def main() -> int:
                     help="fixed walk launch shape 'warps,smem_levels,blocks_per_sm,tile' instead of the autotuner")
     ap.add_argument("--serving-requests", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=20)
+    ap.add_argument("--details", default="bench_details.json",
+                    help="side JSON file for the per-result and per-workload figures ('' = none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -55,7 +55,7 @@ def test_every_launch_shape_gives_the_same_bits(grt, name):
     o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], 3)
     from test_parity_gpu import _assert_fp32_parity
     _assert_fp32_parity(dict(u=outs[0][0], coef=outs[0][1], status=outs[0][2]), o, wl["ntrees"], ctol=1.5e-4,
-                        L=wl["L"], M=wl["M"])
+                        L=wl["L"], M=wl["M"], unpinned=wl.get("past_blowup"))
     with pytest.raises(grt.GrtError):
         grt.grt_plan_set_config(plan, [5, 0, 0, 512])
     plan.close()

@@ -57,10 +57,14 @@ def pade_error_bound(a, L, M, da):
     return b
 
 
-def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5, L=None, M=None):
-    """Pade value within rtol * max(|u|, sum |a_n|) -- or, where the Pade is ill-conditioned (past
-    blow-up, near a pole), within twice its first-order error bound from the coefficient budget;
-    a_n within ctol of the mean |W| of its order."""
+def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5, L=None, M=None, unpinned=None):
+    """Pade value within rtol * max(|u|, sum |a_n|), and a_n within ctol of the mean |W| of its order.
+
+    The Pade value may miss rtol only at a point whose value has no external truth: the oracle
+    flags its Pade as singular or next to a pole (PADE_SINGULAR, PADE_POLE_NEAR), or the workload
+    marks it past blow-up (`unpinned`, a mask).  There, where the approximant is ill-conditioned,
+    it must still lie within twice the first-order error bound of the coefficient budget.  Returns
+    the indices of the points that took that escape, so that callers assert how many did."""
     N = np.maximum(np.asarray(nt, float), 1.0)[:, None]
     scale_coef = o["sa"] / N  # mean |W| of each order: the natural scale of a_n
     err_c = np.abs(g["coef"] - o["coef"])
@@ -72,24 +76,28 @@ def _assert_fp32_parity(g, o, nt, rtol=1e-5, ctol=3e-5, L=None, M=None):
     K = o["coef"].shape[1] - 1
     if L is None:
         L, M = K // 2, K - K // 2
-    conditioned = []
+    flagged = (np.asarray(o["status"]) & 3) != 0
+    if unpinned is not None:
+        flagged = flagged | np.asarray(unpinned, bool)
+    escaped = []
     for i in bad_u:
+        if not flagged[i]:
+            continue
         bound = pade_error_bound(o["coef"][i], L, M, ctol * scale_coef[i] + FP32_FLOOR)
         if du[i] <= 2.0 * bound:
-            conditioned.append(int(i))
-    bad_u = np.array([i for i in bad_u if int(i) not in conditioned], dtype=int)
-    assert len(conditioned) <= max(2, len(du) // 4), conditioned
+            escaped.append(int(i))
+    bad_u = np.array([i for i in bad_u if int(i) not in escaped], dtype=int)
     bad_c = np.argwhere(~(err_c <= ctol * scale_coef + FP32_FLOOR))
     high = (g["status"] & 8) != (o["status"] & 8)
     msg = (f"max u ratio {np.max(ratio_u):.3g}, max coef ratio {np.max(ratio_c):.3g}; "
-           f"u fails {[(int(i), g['u'][i], o['u'][i], scale_u[i]) for i in bad_u[:6]]}; "
+           f"u fails {[(int(i), g['u'][i], o['u'][i], scale_u[i], int(o['status'][i])) for i in bad_u[:6]]}; "
            f"coef fails {[tuple(map(int, ij)) for ij in bad_c[:6]]}; "
            f"status g {g['status'][:12]} o {o['status'][:12]}")
     assert bad_u.size == 0 and bad_c.size == 0 and not high.any(), msg
     # Pade degeneracy decisions (G9 reading) may differ only where the coefficients differ
     pade_diff = (g["status"] & 3) != (o["status"] & 3)
     assert pade_diff.sum() <= max(1, len(pade_diff) // 50), msg
-    return conditioned
+    return escaped
 
 
 # ---------------------------------------------------------------------------
@@ -190,13 +198,13 @@ def test_unit_profile_leaves_gpu_trees_unchanged(grt):
 def test_variable_coefficient_point_solve(grt):
     wl = workloads.subsample(workloads.workload_var_coef_2d(), 24, ntrees=3000)
     g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
-    _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"])
+    assert _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"]) == []
 
 
 def test_euler_point_solve(grt):
     wl = workloads.subsample(workloads.workload_drift_2d(), 24, ntrees=3000)
     g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
-    _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"])
+    assert _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"]) == []
 
 
 def test_strategy_a_fp32_topology_mismatches_are_rare(grt):
@@ -237,7 +245,9 @@ def test_kpp_1d_full_workload_fp64(grt):
 def test_point_solve_fp32(grt, name, ntrees, ctol):
     wl = workloads.subsample(workloads.WORKLOADS[name](), 24, ntrees=ntrees)
     g, o = _solve_both(grt, wl["problem"], wl["x"], wl["t"], wl["ntrees"], wl["K"], wl["L"], wl["M"], wl["seed"])
-    _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol, L=wl["L"], M=wl["M"])
+    esc = _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol, L=wl["L"], M=wl["M"], unpinned=wl.get("past_blowup"))
+    if name == "sin_2d":
+        assert esc == []
 
 
 def test_edge_budgets_and_orders(grt):
@@ -366,7 +376,35 @@ def test_full_size_sin_2d_sampled_points(grt):
         o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], wl["K"], wl["L"],
                          wl["M"], wl["seed"], point_base=i)
         gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
-        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], L=wl["L"], M=wl["M"])
+        assert _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], L=wl["L"], M=wl["M"]) == []
+
+
+def test_full_size_sin_2d_every_point(grt):
+    """Every one of sin_2d's 512 point solves at its full budget (1e5 trees each), in the autotuned
+    launch shape the benchmark times, against the oracle on the same streams: the Pade value within
+    1e-5 max(|u|, sum |a_n|) at every point, with no escape (sin_2d has no singular, pole-near or
+    past-blow-up point)."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.workload_sin_2d()
+    n, K = wl["x"].shape[0], wl["K"]
+    dev = torch.device("cuda:0")
+    x, t = torch.from_numpy(wl["x"]).to(dev), torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = grt.grt_create(wl["problem"], 0)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, wl["L"], wl["M"])
+    grt.grt_plan_autotune(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    torch.cuda.synchronize()
+    g = dict(u=u.cpu().numpy(), coef=coef.cpu().numpy(), status=st.cpu().numpy())
+    plan.close()
+    ctx.close()
+    o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], K, wl["L"], wl["M"], wl["seed"])
+    assert not np.any(o["status"] & 3)
+    assert _assert_fp32_parity(g, o, wl["ntrees"], L=wl["L"], M=wl["M"]) == []
+    scale = np.maximum(np.abs(o["u"]), np.abs(o["coef"]).sum(axis=1))
+    assert np.max(np.abs(g["u"] - o["u"]) / scale) <= 1e-5
 
 
 def test_invalid_coefficient_profiles_rejected(grt):
@@ -450,7 +488,10 @@ def test_full_size_workloads_sampled_points(grt, name, ctol):
         o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], K, wl["L"],
                          wl["M"], wl["seed"], point_base=i)
         gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
-        _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], ctol=ctol, L=wl["L"], M=wl["M"])
+        pb_mask = wl["past_blowup"][i:i + 1] if "past_blowup" in wl else None
+        esc = _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], ctol=ctol, L=wl["L"], M=wl["M"], unpinned=pb_mask)
+        if name in ("var_coef_2d", "drift_2d"):
+            assert esc == []
 
 
 def test_pade_error_parity_and_calibration(grt):

@@ -136,7 +136,12 @@ def workload_uneven_2d(seed: int = 0) -> dict:
     n = x.shape[0]
     t = rng.uniform(0.1, 2.0, size=n)
     ntrees = np.exp(rng.uniform(math.log(1e3), math.log(1e6), size=n)).astype(np.uint64)
-    return dict(name="uneven_2d", problem=problem_uneven_2d(), x=x, t=t, ntrees=ntrees, K=16, L=8, M=8, seed=0)
+    # u0 lies in [1, 2] and f = u^2: by comparison with the ODE u' = u^2 from 1 and from 2 the
+    # solution blows up somewhere in t in [1/2, 1] and everywhere by t = 1, so points at t >= 1/2
+    # may lie past blow-up, where the Pade value continues the series and no PDE value exists
+    past_blowup = t >= 0.5
+    return dict(name="uneven_2d", problem=problem_uneven_2d(), x=x, t=t, ntrees=ntrees, K=16, L=8, M=8, seed=0,
+                past_blowup=past_blowup)
 
 
 def workload_pdd_3d() -> dict:
@@ -204,6 +209,8 @@ def subsample(wl: dict, npoints: int, ntrees: int | None = None, stride: int | N
         nt = np.minimum(nt, np.uint64(ntrees)).astype(np.uint64)
     out["ntrees"] = nt
     out["index"] = idx
+    if "past_blowup" in wl:
+        out["past_blowup"] = np.asarray(wl["past_blowup"])[idx].copy()
     return out
 
 
