@@ -321,9 +321,10 @@ int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *
 #define GRT_NOALLOC_MAX_TREES 524288ull /* summed over the call's points */
 
 /* Point solve that allocates no memory (the paper has no counterpart: this is
- * a service for callers that cannot allocate device memory when they solve,
- * e.g. code running under a CUDA stream capture, where cudaMalloc is not
- * allowed, or an application whose own pool allocator owns the device memory).
+ * a service for callers that cannot allocate device memory when they solve:
+ * an application whose own pool allocator has reserved the device memory, or
+ * code on a latency-critical path where a cudaMalloc, which may synchronise
+ * the device, is not acceptable).
  * Same arguments and results as grt_plan_execute, without a plan: d_x [n][dim],
  * d_t [n], d_u [n], d_coef / d_se [n][K+1] (may be NULL), d_status [n] (may be
  * NULL) are DEVICE arrays owned by the caller; ntrees [n] is a HOST array.  The
@@ -333,9 +334,11 @@ int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *
  * else GRT_EINVAL with a message.  The first call on a device looks up the
  * work area's device address; make that first call before any stream capture.
  * Enqueued on `stream` (NULL = legacy default stream); returns after enqueueing.
- * All calls share the one work area: calls whose GPU work can overlap in time
- * (different streams, or different host threads) race and must be serialised
- * by the caller. */
+ * All calls share the one work area, which keeps the last call's contents
+ * (each call clears what must start at zero): calls whose GPU work can overlap
+ * in time (different streams, or different host threads) race and must be
+ * serialised by the caller.  The host-side part of concurrent calls is
+ * serialised by the library. */
 int grt_solve_noalloc(grt_ctx *ctx, int64_t n, const double *d_x, const double *d_t, const uint64_t *ntrees, int K,
                       int L, int M, uint64_t seed, uint64_t point_base, double *d_u, double *d_coef, double *d_se,
                       int32_t *d_status, void *stream);

@@ -862,12 +862,16 @@ int grt_trees(grt_ctx *c, const double *x, double t, uint64_t point_index, uint6
 // Solve without any device allocation (grt_solve_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a solve:
-// code running under a CUDA stream capture (cudaMalloc is not capturable), or
-// a host that has handed all device memory to its own pool allocator.  For
-// them the whole work area of a solve lives in one fixed-size array of device
+// an application whose own pool allocator has reserved the device memory (a
+// framework's caching allocator holding the GPU, a host that grants each
+// library a fixed share), or code on a latency-critical path where a
+// cudaMalloc, which may synchronise the device, is not acceptable.  For them
+// the whole work area of a solve lives in one fixed-size array of device
 // memory that belongs to the library (every GPU that loads it holds the array
 // until the process exits).  The array is shared by every call, so calls whose
-// GPU work overlaps in time race on it.
+// GPU work overlaps in time race on it.  The host-side layout of a call is
+// built in file-scope arrays (not on the caller's stack, which may be small)
+// under one mutex held until the call has enqueued its copies.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -896,12 +900,17 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 constexpr int kNaMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[kNaMaxDevices] = {};
+// the host-side work layout of the call in progress (guarded by g_noalloc_mutex); the
+// host-to-device copies below read these pageable arrays before cudaMemcpyAsync returns
+uint32_t g_na_prefix[GRT_NOALLOC_MAX_POINTS + 1], g_na_nt32[GRT_NOALLOC_MAX_POINTS],
+    g_na_cprefix[GRT_NOALLOC_MAX_POINTS + 1];
+unsigned long long g_na_tprefix[GRT_NOALLOC_MAX_POINTS + 1];
 
 // Device address of the work area on the current device `dev`, looked up once
-// per device (on the first call of grt_solve_noalloc on that device).
+// per device (on the first call of grt_solve_noalloc on that device).  The
+// caller holds g_noalloc_mutex.
 cudaError_t noalloc_scratch(int dev, unsigned char **out) {
   if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
     void *ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -926,9 +935,10 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
   if (n == 0) return GRT_OK;
   if (!ntrees || !d_x || !d_t || !d_u) return c->set_error(GRT_EINVAL, "x, t, ntrees and u must be non-NULL");
   if (point_base + (uint64_t)n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
-  // work layout on the host, in fixed-size arrays on this thread's stack (no heap)
-  uint32_t prefix[GRT_NOALLOC_MAX_POINTS + 1], nt32[GRT_NOALLOC_MAX_POINTS], cprefix[GRT_NOALLOC_MAX_POINTS + 1];
-  unsigned long long tprefix[GRT_NOALLOC_MAX_POINTS + 1];
+  // work layout on the host, in the library's fixed arrays (no heap, nothing on the caller's stack)
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  uint32_t *prefix = g_na_prefix, *nt32 = g_na_nt32, *cprefix = g_na_cprefix;
+  unsigned long long *tprefix = g_na_tprefix;
   uint64_t items = 0, trees = 0, chunks = 0, recs = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");

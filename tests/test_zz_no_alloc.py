@@ -1,8 +1,9 @@
 """grt_solve_noalloc: the point solve for callers that cannot allocate device memory.
 
-Such callers (code running under a CUDA stream capture, where cudaMalloc is not
-allowed, or an application whose pool allocator owns the device memory) get a
-solve whose whole work area is a fixed array the library keeps on the device.
+Such callers (an application whose own pool allocator has reserved the device
+memory, or a latency-critical path where a possibly synchronising cudaMalloc is
+not acceptable) get a solve whose whole work area is a fixed array the library
+keeps on the device.
 This file is collected last so that a run stopping at its first failure has
 already run every other test; it also passes alone in a fresh process.
 """
@@ -46,6 +47,37 @@ def test_noalloc_matches_the_allocating_solve_on_two_calls(grt):
         assert np.all(np.abs(u.cpu().numpy() - ref["u"]) <= 1e-12 * scale), call
         assert np.allclose(coef.cpu().numpy(), ref["coef"], rtol=1e-12, atol=1e-300), call
         assert np.allclose(se.cpu().numpy(), ref["se"], rtol=1e-12, atol=1e-300), call
+        assert np.array_equal(st.cpu().numpy(), ref["status"]), call
+    ctx.close()
+
+
+def test_noalloc_at_its_limits_matches_the_allocating_solve(grt):
+    """Exactly at both limits: 4096 points holding 524288 trees, most of them one-tree points (the
+    most record padding, each point's records starting on a multiple of 4) plus points of 8193
+    trees (two binning chunks each for 8193 trees: the most chunks), in two consecutive calls."""
+    torch = pytest.importorskip("torch")
+    n = grt.NOALLOC_MAX_POINTS
+    nt = np.ones(n, np.uint64)
+    nt[:63] = 8193
+    nt[-1] += grt.NOALLOC_MAX_TREES - int(nt.sum())
+    assert int(nt.sum()) == grt.NOALLOC_MAX_TREES and nt[-1] >= 1
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-3.0, 3.0, size=(n, 2))
+    t = rng.uniform(0.1, 1.0, size=n)
+    pb = workloads.problem_sin_2d()
+    K, L, M = 10, 5, 5
+    ctx = grt.grt_create(pb, 0)
+    ref = grt.grt_solve(ctx, x, t, nt, K, L, M, 21, 0)
+    dev = torch.device("cuda:0")
+    xd, td = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
+    for call in range(2):
+        u = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+        coef = torch.full((n, K + 1), float("nan"), dtype=torch.float64, device=dev)
+        st = torch.full((n,), -1, dtype=torch.int32, device=dev)
+        grt.grt_solve_noalloc(ctx, xd, td, nt, K, L, M, 21, 0, u, coef, None, st)
+        torch.cuda.synchronize()
+        assert np.array_equal(coef.cpu().numpy(), ref["coef"]), call
+        assert np.array_equal(u.cpu().numpy(), ref["u"], equal_nan=True), call
         assert np.array_equal(st.cpu().numpy(), ref["status"]), call
     ctx.close()
 
