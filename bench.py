@@ -282,6 +282,28 @@ def reference_arm(args) -> int:
 # ---------------------------------------------------------------------------
 # the other workloads: uneven budgets (4096 interface points) and the 3-D PDD planes
 # ---------------------------------------------------------------------------
+def pade_health(grt, ctx, plan, x, t, seed: int, K: int, L: int, M: int, tmask=None) -> dict:
+    """How many point values the Pade has spoiled: points flagged PADE_POLE_NEAR (|Q(1)| < 1e-8) or
+    PADE_SINGULAR, and points whose first-order statistical error (grt_pade_error from the standard
+    errors) exceeds 1e-2 -- over all points, or over those of `tmask` (a boolean mask)."""
+    import torch
+
+    dev = x.device
+    n = x.shape[0]
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    se = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    err = torch.empty(n, dtype=torch.float64, device=dev)
+    grt.grt_plan_execute(plan, x, t, seed, 0, u, coef, se, st)
+    grt.grt_pade_error(ctx, coef, se, L, M, err)
+    torch.cuda.synchronize(dev)
+    sth, eh = st.cpu().numpy(), err.cpu().numpy()
+    m = np.ones(n, bool) if tmask is None else np.asarray(tmask, bool)
+    return {"points": int(m.sum()), "pole_near": int(((sth & 2) != 0)[m].sum()),
+            "singular": int(((sth & 1) != 0)[m].sum()), "err_over_1e-2": int((~(eh <= 1e-2))[m].sum()),
+            "err_median": float(np.median(eh[m])) if m.any() else None}
+
 def workload_bench(grt, dev_index: int, name: str, steps: int) -> dict:
     import torch
 
@@ -315,9 +337,11 @@ def workload_bench(grt, dev_index: int, name: str, steps: int) -> dict:
     nodes, splits, pruned = grt.grt_plan_counters(plan)
     trees = float(np.sum(wl["ntrees"]))
     finite = bool(torch.isfinite(u).all().item())
+    health = pade_health(grt, ctx, plan, x, t, wl["seed"], K, wl["L"], wl["M"])
     plan.close()
     ctx.close()
     return {"trees_per_s": trees / (ms / 1e3), "points_per_s": n / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+            "pade_health": health,
             "walk_ms": float(np.mean(wms)), "finalize_ms": float(np.mean(fms)), "points": n, "trees": trees,
             "nodes": nodes, "pruned_trees": pruned, "K": K, "L": wl["L"], "M": wl["M"],
             "walk_config": dict(zip(["warps", "smem_levels", "blocks_per_sm", "tile"], cfg)), "finite_output": finite}
@@ -389,6 +413,9 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
     mc = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
     pd = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
     finite = bool(torch.isfinite(out).all().item())
+    # the interface values the Pade has spoiled, at the last time level (t = T = 1) and over all levels
+    health_T = pade_health(grt, ctx, plan, dx, dtt, 0, wl["K"], wl["L"], wl["M"], tmask=np.isclose(t, g["T"]))
+    health_all = pade_health(grt, ctx, plan, dx, dtt, 0, wl["K"], wl["L"], wl["M"])
     plan.close()
     ctx.close()
     nsub = int(np.prod(g["sub"]))
@@ -410,7 +437,7 @@ def pdd_bench(grt, dev_index: int, steps: int) -> dict:
                                            f"the subdomain blocks run on min(blocks, {sms}) SMs"},
             "subdomain_unknowns": int(np.prod([c - 1 for c in g["cells"]])), "cn_steps": g["nsteps"],
             "point_solve_ms": mc, "pdd_stage_ms": pd, "total_ms": mc + pd, "steps": steps,
-            "finite_output": finite,
+            "finite_output": finite, "pade_health_at_T": health_T, "pade_health_all_levels": health_all,
             "description": ("u_t = 0.1 Lap u + u - u^3, u0 = prod tanh(x_i - 2) on [0,4]^3 cut into 4x4x4 subdomains; "
                             "15 planes (outer faces = probabilistic artificial boundaries) x 17^2 nodes x 4 time levels "
                             "= 17340 point solves of 1e5 trees, K = 12 [6/6]; not-a-knot tensor spline to the 65^3 "
@@ -461,11 +488,13 @@ def _serve_trace(grt, dev: int, probs: dict, ctxs: dict, trace: list) -> dict:
     st1 = grt.grt_server_stats(server)
     server.close()
     points = int(sum(len(r["t"]) for r in trace))
+    shared = st1["shared_launches"] - st0["shared_launches"]
     trees = float(sum(float(r["ntrees"].sum()) for r in trace))
     wall = t_end - t0
     return {"lat": lat, "requests": len(trace), "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
             "mean_ms": 1e3 * float(np.mean(lat)), "points_per_s": points / wall, "trees_per_s": trees / wall,
-            "wall_s": wall, "steps": st1["steps"] - st0["steps"], "launches": st1["launches"] - st0["launches"]}
+            "wall_s": wall, "steps": st1["steps"] - st0["steps"], "launches": st1["launches"] - st0["launches"],
+            "shared_launches": shared}
 
 
 def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, plain_requests: int,
@@ -487,12 +516,12 @@ def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, p
         over = _serve_trace(grt, dev, probs, ctxs, workloads.serving_trace(overload_requests, 2000.0, seed=1))
         over.pop("lat")
         out["at_configured_rate"] = dict(trace=f"{overload_requests} Poisson requests at 2000 req/s, same mix", **over)
-    # plain path: one FP64 solve per request, first come first served, same arrivals
+    # plain path: one FP64 launch per point (grt_solve_plain), requests first come first served, same arrivals
     ctx64 = {k: grt.grt_create(dict(v["problem"], precision="fp64"), dev) for k, v in probs.items()}
     for k, v in probs.items():  # warm-up
         d = v["problem"]["dim"]
-        grt.grt_solve(ctx64[k], np.zeros((2, d)), np.full(2, 0.5), np.full(2, 1000, np.uint64), v["K"], v["L"],
-                      v["M"], 99, want_coef=False, want_se=False)
+        grt.grt_solve_plain(ctx64[k], np.zeros((2, d)), np.full(2, 0.5), np.full(2, 1000, np.uint64), v["K"], v["L"],
+                            v["M"], 99, want_coef=False, want_se=False)
     plat, ppoints, ptrees = [], 0, 0.0
     t0 = time.perf_counter()
     for r in trace[:plain_requests]:
@@ -500,8 +529,8 @@ def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, p
         if now < r["arrival"]:
             time.sleep(r["arrival"] - now)
         v = probs[r["key"]]
-        grt.grt_solve(ctx64[r["key"]], r["x"], r["t"], r["ntrees"], v["K"], v["L"], v["M"], r["seed"],
-                      r["point_base"], want_coef=False, want_se=False)
+        grt.grt_solve_plain(ctx64[r["key"]], r["x"], r["t"], r["ntrees"], v["K"], v["L"], v["M"], r["seed"],
+                            r["point_base"], want_coef=False, want_se=False)
         plat.append(time.perf_counter() - t0 - r["arrival"])
         ppoints += len(r["t"])
         ptrees += float(r["ntrees"].sum())
@@ -510,7 +539,8 @@ def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, p
     pwall = time.perf_counter() - t0
     m = len(plat)
     out["plain"] = {
-        "kind": "one FP64 grt_solve (walk + finalize launch) per request, first come first served, same arrivals",
+        "kind": "grt_solve_plain: one FP64 kernel launch per point (walk, block reductions and Pade in the launch), "
+                "requests first come first served, same arrivals",
         "requests": m, "p50_ms": 1e3 * _pct(plat, 50), "p99_ms": 1e3 * _pct(plat, 99),
         "points_per_s": ppoints / pwall, "trees_per_s": ptrees / pwall,
         "batched_p50_ms_same_requests": 1e3 * _pct(lat[:m], 50),
@@ -806,6 +836,9 @@ def gpu_arm(args) -> int:
         pp = wls["pdd_3d_pipeline"]
         line["pdd_3d_pipeline_ms"] = {"point_solves": round(pp["point_solve_ms"], 3),
                                       "pdd_stage": round(pp["pdd_stage_ms"], 3)}
+        h = wls["pdd_3d"]["pade_health"]
+        line["pdd_3d_pade_at_t1"] = {"points": h["points"], "pole_near": h["pole_near"],
+                                     "err_over_1e-2": h["err_over_1e-2"]}
     if not args.no_serving and world == 1:
         srv = serving_bench(grt, gpu, value / world, args.serving_requests, args.plain_requests,
                             float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
@@ -837,7 +870,7 @@ def gpu_arm(args) -> int:
 def serving_summary(srv: dict) -> dict:
     """The serving figures the headline metric names: p50/p99 latency and points/s of the batched
     server against the plain one-launch-per-point FP64 path, on the same requests."""
-    out = {k: srv.get(k) for k in ("requests", "p50_ms", "p99_ms", "points_per_s", "trees_per_s")}
+    out = {k: srv.get(k) for k in ("requests", "p50_ms", "p99_ms", "points_per_s", "trees_per_s", "shared_launches")}
     pl = srv.get("plain") or {}
     out["plain"] = {k: pl.get(k) for k in ("requests", "p50_ms", "p99_ms", "points_per_s",
                                            "batched_p50_ms_same_requests", "batched_p99_ms_same_requests")}
@@ -851,7 +884,8 @@ def serving_summary(srv: dict) -> dict:
 HEADLINE_MAX_BYTES = 2400
 # optional keys dropped, in this order, should the headline line outgrow HEADLINE_MAX_BYTES (all of them
 # stay in the side file)
-HEADLINE_OPTIONAL = (("serving", "at_configured_rate"), ("pdd_3d_pipeline_ms",), ("workloads_trees_per_s",),
+HEADLINE_OPTIONAL = (("serving", "at_configured_rate"), ("pdd_3d_pade_at_t1",), ("pdd_3d_pipeline_ms",),
+                     ("workloads_trees_per_s",),
                      ("roofline", "graph_ms_per_step"), ("serving",))
 
 

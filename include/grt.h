@@ -54,7 +54,6 @@ extern "C" {
 #define GRT_EINVAL (-1)   /* an argument is outside its documented range     */
 #define GRT_ENOMEM (-2)   /* device or pinned host memory could not be had   */
 #define GRT_EDEVICE (-3)  /* a CUDA call failed (no device, launch error...) */
-#define GRT_ETIMEOUT (-4) /* a bounded device wait ran out                   */
 #define GRT_ENOTSUP (-5)  /* valid request the library does not support      */
 #define GRT_EAGAIN 1      /* (grt_poll) the request has not finished yet      */
 
@@ -105,7 +104,7 @@ extern "C" {
 #define GRT_STATUS_PADE_SINGULAR 1  /* a Pade pivot was below 1e-14 of the largest matrix
                                        entry: the type was lowered [L-1/M-1] until solvable */
 #define GRT_STATUS_PADE_POLE_NEAR 2 /* |Q(1)| < 1e-8                                   */
-#define GRT_STATUS_SERIES_PARTIAL 4 /* fewer trees than requested contributed          */
+#define GRT_STATUS_SERIES_PARTIAL 4 /* fewer trees than requested contributed (grt_cancel) */
 #define GRT_STATUS_HIGH_PRUNE 8     /* more than 1% of the trees had Ne > K            */
 
 /* Problem description (copied by grt_create). */
@@ -166,6 +165,22 @@ const char *grt_last_error(const grt_ctx *ctx);
 int grt_solve(grt_ctx *ctx, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K,
               int L, int M, uint64_t seed, uint64_t point_base, double *u_out, double *coef_out,
               double *se_out, int32_t *status_out);
+
+/* The plain FP64 point solve: one kernel launch per point, same arguments and
+ * HOST arrays as grt_solve (the FP64 comparison path of the serving figures;
+ * the walk runs in FP64 whatever the context's precision).  For each point, in
+ * order, one launch of min(ceil(N_i / 128), 8 x SMs) blocks of 128 threads:
+ * thread g walks trees g, g + G, ... (G threads) of the point's stream (the
+ * algorithm after Sec. 2.1 Eq. recursion / Sec. 2.2), adds each tree's weight
+ * to its own FP64 per-order sums, the sums are reduced by warp shuffles and
+ * then per block in a fixed order, and the launch's last block adds the block
+ * partials in block order, forms a_n and SE_n (Sec. 2.4, Eq.
+ * simplecase_discrete) and the FP64 [L/M] Pade (Sec. 2.1 end, Sec. 2.4).
+ * Results agree with grt_solve on an FP64 context up to the rounding of the
+ * different summation order.  GRT_EINVAL as grt_solve; synchronous. */
+int grt_solve_plain(grt_ctx *ctx, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K,
+                    int L, int M, uint64_t seed, uint64_t point_base, double *u_out, double *coef_out,
+                    double *se_out, int32_t *status_out);
 
 /* Device-resident form, for callers that keep their points in device memory
  * and launch many solves of the same shape (e.g. under a CUDA graph).
@@ -282,13 +297,16 @@ int grt_trees(grt_ctx *ctx, const double *x, double t, uint64_t point_index, uin
  * most `step_trees` trees taken from all admitted requests, smallest remaining
  * work first, in ranges that start on a point's 8192-tree boundaries; requests
  * of one problem, K, L, M and seed share one walk and one binning launch per
- * step.  A point's result is identical, bit for bit, to grt_solve of the same
- * point (same point_base + index and seed), alone or in any mix.
+ * step; the groups of one step run concurrently on several streams.  A point's
+ * result is identical, bit for bit, to grt_solve of the same point (same
+ * point_base + index and seed), alone or in any mix.  Batching happens at step
+ * boundaries: a request that arrives while others run joins the next step
+ * (steps of at most step_trees trees, a few milliseconds at full load).
  * Contexts passed to grt_submit must outlive their requests. */
 typedef struct grt_server grt_server;
 
 /* mem_budget_bytes: device memory for step buffers and resident state (at least
- * step_trees x 9 bytes + 80 bytes per step point + 1 MB; step points =
+ * 9 (step_trees + 4 P + 64) + 312 P + 65 KB + 1 MB bytes, P = step points =
  * clamp(step_trees / 256, 4096, 2^20)); step_trees: trees per step (0: 2^27).
  * GRT_EINVAL if the budget is too small, GRT_ENOMEM / GRT_EDEVICE on failure. */
 int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees, grt_server **out);
@@ -312,9 +330,37 @@ int grt_submit(grt_server *s, grt_ctx *ctx, int64_t n, const double *x, const do
 int grt_poll(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
              int32_t *status_out, double *latency_s);
 
-/* Steps run, trees walked, kernel launches, resident bytes, pending and active requests. */
+/* Per-request figures returned by grt_poll_ex. */
+typedef struct grt_request_info {
+    double latency_s;          /* submit to completion                                    */
+    uint64_t shared_launches;  /* walk launches that also walked another request's trees  */
+    uint64_t shared_steps;     /* scheduler steps that also ran another request's trees   */
+    int32_t cancelled;         /* grt_cancel was called before the request finished       */
+} grt_request_info;
+
+/* grt_poll with the number of trees each point's estimate used: ntrees_done [n]
+ * (may be NULL; N_i unless the request was cancelled) and *info (may be NULL). */
+int grt_poll_ex(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
+                int32_t *status_out, uint64_t *ntrees_done, grt_request_info *info);
+
+/* Stop a request early (a caller's deadline: grt_poll with a timeout, then
+ * grt_cancel).  The request takes no more trees after the step in progress;
+ * each point that has not received all its trees is then completed from the
+ * trees already binned -- N_done of them, the first N_done trees of the point's
+ * stream, a multiple of 8192 -- and gets GRT_STATUS_SERIES_PARTIAL: its a_n,
+ * SE_n and Pade value are those of grt_solve with N_i = N_done, bit for bit
+ * (the trees are independent samples, Sec. 3, so the estimate stays unbiased,
+ * with the larger error of N_done trees).  A request still waiting for
+ * admission ends with N_done = 0 (u = 0, a_n = 0).  Poll it as usual.  GRT_OK
+ * also for a request that has already finished; GRT_EINVAL for an unknown id. */
+int grt_cancel(grt_server *s, uint64_t request_id);
+
+/* Steps run, trees walked, kernel launches, resident bytes, pending and active
+ * requests, walk launches that batched trees of several requests, requests
+ * cancelled before they finished (any output may be NULL). */
 int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *launches, uint64_t *resident_bytes,
-                     uint64_t *pending_requests, uint64_t *active_requests);
+                     uint64_t *pending_requests, uint64_t *active_requests, uint64_t *shared_launches,
+                     uint64_t *cancelled_requests);
 
 /* Limits of grt_solve_noalloc. */
 #define GRT_NOALLOC_MAX_POINTS 4096

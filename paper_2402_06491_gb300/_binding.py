@@ -19,7 +19,7 @@ MAX_DIM = 3
 MAX_DEG = 15
 MAX_K = 16
 
-OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, ENOTSUP, EAGAIN = 0, -1, -2, -3, -4, -5, 1
+OK, EINVAL, ENOMEM, EDEVICE, ENOTSUP, EAGAIN = 0, -1, -2, -3, -5, 1
 STRATEGY = {"A": 0, "B": 1}
 ARITY_LAW = {"uniform": 0, "abs": 1}
 PRECISION = {"fp32": 0, "fp64": 1}
@@ -57,6 +57,15 @@ class grt_problem(ctypes.Structure):
     ]
 
 
+class grt_request_info(ctypes.Structure):
+    _fields_ = [
+        ("latency_s", ctypes.c_double),
+        ("shared_launches", ctypes.c_uint64),
+        ("shared_steps", ctypes.c_uint64),
+        ("cancelled", ctypes.c_int32),
+    ]
+
+
 class grt_pdd_grid(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int32),
@@ -90,6 +99,7 @@ def _load():
         "grt_destroy": ([_vp], None),
         "grt_last_error": ([_vp], ctypes.c_char_p),
         "grt_solve": ([_vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, f64p, f64p, f64p, i32p], i32),
+        "grt_solve_plain": ([_vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, f64p, f64p, f64p, i32p], i32),
         "grt_plan_create": ([_vp, i64, u64p, i32, i32, i32, _P(_vp)], i32),
         "grt_plan_execute": ([_vp, _vp, _vp, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
         "grt_plan_counters": ([_vp, u64p, u64p, u64p], i32),
@@ -113,7 +123,9 @@ def _load():
         "grt_server_last_error": ([_vp], ctypes.c_char_p),
         "grt_submit": ([_vp, _vp, i64, f64p, f64p, u64p, i32, i32, i32, u64, u64, u64p], i32),
         "grt_poll": ([_vp, u64, i32, f64p, f64p, f64p, i32p, f64p], i32),
-        "grt_server_stats": ([_vp, u64p, u64p, u64p, u64p, u64p, u64p], i32),
+        "grt_poll_ex": ([_vp, u64, i32, f64p, f64p, f64p, i32p, u64p, _P(grt_request_info)], i32),
+        "grt_cancel": ([_vp, u64], i32),
+        "grt_server_stats": ([_vp, u64p, u64p, u64p, u64p, u64p, u64p, u64p, u64p], i32),
         "grt_spline_grid": ([_vp, i32, i32p, f64p, f64p, i32p, f64p, i64, _vp, _vp, _vp], i32),
         "grt_pdd_points": ([_P(grt_pdd_grid), i64, f64p, f64p, _P(ctypes.c_int64)], i32),
         "grt_pdd_solve": ([_vp, _P(grt_pdd_grid), _vp, _vp, _vp], i32),
@@ -294,6 +306,26 @@ def grt_solve(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int, poi
     rc = lib.grt_solve(ctx.handle, n, _ptr(xs, ctypes.c_double), _ptr(ts, ctypes.c_double),
                        _ptr(nt, ctypes.c_uint64), K, L, M, int(seed), int(point_base), _ptr(u, ctypes.c_double),
                        _ptr(coef, ctypes.c_double), _ptr(se, ctypes.c_double), _ptr(st, ctypes.c_int32))
+    _check(rc, ctx.handle)
+    return dict(u=u, coef=coef, se=se, status=st)
+
+
+def grt_solve_plain(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int, point_base: int = 0,
+                    want_coef: bool = True, want_se: bool = True) -> dict:
+    """The plain FP64 solve, one kernel launch per point (host arrays, synchronous)."""
+    lib = _load()
+    d = ctx.dim
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
+    n = xs.shape[0]
+    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
+    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    u = np.empty(n, np.float64)
+    coef = np.empty((n, K + 1), np.float64) if want_coef else None
+    se = np.empty((n, K + 1), np.float64) if want_se else None
+    st = np.empty(n, np.int32)
+    rc = lib.grt_solve_plain(ctx.handle, n, _ptr(xs, ctypes.c_double), _ptr(ts, ctypes.c_double),
+                             _ptr(nt, ctypes.c_uint64), K, L, M, int(seed), int(point_base), _ptr(u, ctypes.c_double),
+                             _ptr(coef, ctypes.c_double), _ptr(se, ctypes.c_double), _ptr(st, ctypes.c_int32))
     _check(rc, ctx.handle)
     return dict(u=u, coef=coef, se=se, status=st)
 
@@ -544,10 +576,37 @@ def grt_poll(server: Server, request_id: int, timeout_ms: int = -1):
     return dict(u=u, coef=coef, se=se, status=st, latency_s=lat.value)
 
 
+def grt_poll_ex(server: Server, request_id: int, timeout_ms: int = -1):
+    """grt_poll plus the trees each point's estimate used (ntrees_done) and the request's sharing figures."""
+    lib = _load()
+    n, K = server.requests[request_id]
+    u = np.empty(n, np.float64)
+    coef = np.empty((n, K + 1), np.float64)
+    se = np.empty((n, K + 1), np.float64)
+    st = np.empty(n, np.int32)
+    nd = np.empty(n, np.uint64)
+    info = grt_request_info()
+    rc = lib.grt_poll_ex(server.handle, int(request_id), int(timeout_ms), _ptr(u, ctypes.c_double),
+                         _ptr(coef, ctypes.c_double), _ptr(se, ctypes.c_double), _ptr(st, ctypes.c_int32),
+                         _ptr(nd, ctypes.c_uint64), ctypes.byref(info))
+    if rc == EAGAIN:
+        return None
+    del server.requests[request_id]
+    _check_server(rc, server)
+    return dict(u=u, coef=coef, se=se, status=st, ntrees_done=nd, latency_s=info.latency_s,
+                shared_launches=int(info.shared_launches), shared_steps=int(info.shared_steps),
+                cancelled=bool(info.cancelled))
+
+
+def grt_cancel(server: Server, request_id: int) -> None:
+    """Stop a request early: unfinished points end with the trees binned so far (SERIES_PARTIAL)."""
+    _check_server(_load().grt_cancel(server.handle, int(request_id)), server)
+
+
 def grt_server_stats(server: Server) -> dict:
-    vals = [ctypes.c_uint64(0) for _ in range(6)]
+    vals = [ctypes.c_uint64(0) for _ in range(8)]
     _check_server(_load().grt_server_stats(server.handle, *[ctypes.byref(v) for v in vals]), server)
-    keys = ["steps", "trees", "launches", "resident_bytes", "pending", "active"]
+    keys = ["steps", "trees", "launches", "resident_bytes", "pending", "active", "shared_launches", "cancelled"]
     return {k: int(v.value) for k, v in zip(keys, vals)}
 
 
@@ -626,10 +685,12 @@ def grt_spline_grid(ctx: Context, n_nodes, lo, hi, targets, values, out, batch: 
     _check(rc, ctx.handle)
 
 
-EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_plan_create", "grt_plan_execute",
+EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_solve_plain", "grt_plan_create",
+            "grt_plan_execute",
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
             "grt_plan_set_config", "grt_plan_get_config", "grt_set_solve_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
             "grt_pade", "grt_pade_error", "grt_plan_kappa", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
-            "grt_server_last_error", "grt_submit", "grt_poll", "grt_server_stats", "grt_spline_grid",
+            "grt_server_last_error", "grt_submit", "grt_poll", "grt_poll_ex", "grt_cancel", "grt_server_stats",
+            "grt_spline_grid",
             "grt_pdd_points", "grt_pdd_solve", "grt_pdd_solve_range"]

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libgrt.so")
 # (source, object name, extra nvcc flags): grt_walk_u0.cu is compiled once per launch shape
 SOURCES = [("grt_api.cu", "grt_api", []), ("grt_walk.cu", "grt_walk", []), ("grt_walk_feat.cu", "grt_walk_feat", []),
            ("grt_trees.cu", "grt_trees", []), ("grt_finalize.cu", "grt_finalize", []),
-           ("grt_server.cu", "grt_server", []), ("grt_pdd.cu", "grt_pdd", [])]
+           ("grt_server.cu", "grt_server", []), ("grt_pdd.cu", "grt_pdd", []), ("grt_plain.cu", "grt_plain", [])]
 for _w, _s in ((4, 0), (4, 3), (8, 0), (8, 3)):
     SOURCES.append(("grt_walk_u0.cu", f"grt_walk_u0_w{_w}s{_s}",
                     [f"-DGRT_U0_FN=launch_walk_u0_w{_w}s{_s}", f"-DGRT_U0_WARPS={_w}", f"-DGRT_U0_SLEV={_s}"]))

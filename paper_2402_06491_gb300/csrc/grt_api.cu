@@ -5,6 +5,7 @@
 // walk and finalize kernels.  Every step of the solve itself runs on the GPU.
 #include "grt.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -494,6 +495,8 @@ void grt_destroy(grt_ctx *ctx) {
   ctx->dse.release();
   ctx->dstatus.release();
   ctx->pdd_scratch.release();
+  ctx->plain_part.release();
+  ctx->plain_ticket.release();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -539,6 +542,71 @@ int grt_solve(grt_ctx *c, int64_t n, const double *x, const double *t, const uin
                     coef_out ? c->dcoef.as<double>() : nullptr, se_out ? c->dse.as<double>() : nullptr,
                     status_out ? c->dstatus.as<int32_t>() : nullptr, s);
   if (rc != GRT_OK) return rc;
+  GRT_CUDA(c, cudaMemcpyAsync(u_out, c->du.ptr, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (coef_out)
+    GRT_CUDA(c, cudaMemcpyAsync(coef_out, c->dcoef.ptr, (size_t)n * (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (se_out)
+    GRT_CUDA(c, cudaMemcpyAsync(se_out, c->dse.ptr, (size_t)n * (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (status_out)
+    GRT_CUDA(c, cudaMemcpyAsync(status_out, c->dstatus.ptr, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GRT_CUDA(c, cudaStreamSynchronize(s));
+  return GRT_OK;
+}
+
+int grt_solve_plain(grt_ctx *c, int64_t n, const double *x, const double *t, const uint64_t *ntrees, int K, int L,
+                    int M, uint64_t seed, uint64_t point_base, double *u_out, double *coef_out, double *se_out,
+                    int32_t *status_out) {
+  if (!c) return GRT_EINVAL;
+  if (n < 0 || n > 0x7FFFFFFFll) return c->set_error(GRT_EINVAL, "n must be in [0, 2^31)");
+  if (K < 0 || K > GRT_MAX_K) return c->set_error(GRT_EINVAL, "K must be in [0, 16]");
+  if (L < 0 || M < 0 || L + M > K) return c->set_error(GRT_EINVAL, "need L, M >= 0 and L + M <= K");
+  if (n == 0) return GRT_OK;
+  if (!x || !t || !ntrees || !u_out) return c->set_error(GRT_EINVAL, "x, t, ntrees and u_out must be non-NULL");
+  if (point_base + (uint64_t)n - 1 > 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "point_base + n exceeds 2^32");
+  const int dim = c->pb.dim;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(is_finite(t[i]) && t[i] >= 0.0)) return c->set_error(GRT_EINVAL, "t must be finite and >= 0");
+    if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
+    for (int d = 0; d < dim; ++d)
+      if (!is_finite(x[i * dim + d])) return c->set_error(GRT_EINVAL, "x must be finite");
+  }
+  GRT_CUDA(c, cudaSetDevice(c->device));
+  // one launch per point, one thread per tree up to the grid's size (then each thread walks several)
+  const uint64_t max_blocks = 8ull * (uint64_t)c->num_sms;
+  auto blocks_of = [&](uint64_t N) {
+    const uint64_t b = (N + grt::kPlainThreads - 1) / grt::kPlainThreads;
+    return (unsigned)(b < 1 ? 1 : (b > max_blocks ? max_blocks : b));
+  };
+  uint64_t most = 1;
+  for (int64_t i = 0; i < n; ++i) most = std::max<uint64_t>(most, blocks_of(ntrees[i]));
+  GRT_CUDA(c, c->plain_part.ensure((size_t)most * 3 * (K + 2) * sizeof(double)));
+  GRT_CUDA(c, c->plain_ticket.ensure((size_t)n * sizeof(uint32_t)));
+  GRT_CUDA(c, c->du.ensure((size_t)n * sizeof(double)));
+  if (coef_out) GRT_CUDA(c, c->dcoef.ensure((size_t)n * (K + 1) * sizeof(double)));
+  if (se_out) GRT_CUDA(c, c->dse.ensure((size_t)n * (K + 1) * sizeof(double)));
+  if (status_out) GRT_CUDA(c, c->dstatus.ensure((size_t)n * sizeof(int32_t)));
+  cudaStream_t s = c->stream;
+  GRT_CUDA(c, cudaMemsetAsync(c->plain_ticket.ptr, 0, (size_t)n * sizeof(uint32_t), s));
+  grt::WalkParams w = c->base;
+  set_round_keys(w, seed);
+  w.K = K;
+  for (int64_t i = 0; i < n; ++i) {
+    grt::PlainPoint q{};
+    for (int d = 0; d < dim; ++d) q.x[d] = x[i * dim + d];
+    q.t = t[i];
+    q.point = (uint32_t)(point_base + (uint64_t)i);
+    q.ntrees = (uint32_t)ntrees[i];
+    q.K = K;
+    q.L = L;
+    q.M = M;
+    q.part = c->plain_part.as<double>();
+    q.ticket = c->plain_ticket.as<uint32_t>() + i;
+    q.u = c->du.as<double>() + i;
+    q.coef = coef_out ? c->dcoef.as<double>() + (size_t)i * (K + 1) : nullptr;
+    q.se = se_out ? c->dse.as<double>() + (size_t)i * (K + 1) : nullptr;
+    q.status = status_out ? c->dstatus.as<int32_t>() + i : nullptr;
+    GRT_CUDA(c, grt::launch_plain(dim, c->pb.strategy, w, q, blocks_of(ntrees[i]), s));
+  }
   GRT_CUDA(c, cudaMemcpyAsync(u_out, c->du.ptr, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (coef_out)
     GRT_CUDA(c, cudaMemcpyAsync(coef_out, c->dcoef.ptr, (size_t)n * (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));

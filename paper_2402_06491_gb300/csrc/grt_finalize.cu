@@ -3,24 +3,10 @@
 // the FP64 [L/M] Pade approximant at eps = 1 (Sec. 2.1 end, Sec. 2.4).
 #include "grt_device.cuh"
 #include "grt_launch.h"
+#include "grt_pade.cuh"
 #include <math_constants.h>
 
 namespace grt {
-
-// Compensated (Kahan) addition; the explicit round-to-nearest intrinsics keep
-// the compiler from reassociating the correction away.
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-  const float y = __fsub_rn(v, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
-}
-__device__ __forceinline__ void kahan_add(double &s, double &c, double v) {
-  const double y = __dsub_rn(v, c);
-  const double t = __dadd_rn(s, y);
-  c = __dsub_rn(__dsub_rn(t, s), y);
-  s = t;
-}
 
 // Per-order accumulator slot of one binning thread, one 16-byte (float) or
 // 32-byte (double) shared-memory access per record.
@@ -45,132 +31,41 @@ __device__ __forceinline__ void load4(const double *p, double (&w)[4]) {
   w[3] = b.y;
 }
 
-// [L/M] Pade of sum a_n eps^n at eps = 1.  The series is first rescaled,
-// c_n = a_n / rho^n with rho = 2^k, k = max_{j > m} ceil((e_j - e_m)/(j - m)),
-// e_j the binary exponent of a_j and m the first nonzero term: this leaves the
-// approximant unchanged (evaluated at w = rho), is exact in floating point,
-// needs no transcendental function, and keeps every |c_j| within a factor of
-// two of |c_m| or below in the Toeplitz system
-// sum_{j=1..M} c_{L+i-j} beta_j = -c_{L+i}, i = 1..M.  Gaussian
-// elimination with partial pivoting; a pivot at or below 1e-14 times the
-// largest entry lowers the type to [L-1/M-1] (L not below 0) and sets
-// PADE_SINGULAR.  |Q(1)| < 1e-8 sets PADE_POLE_NEAR.
-
-// Integer forms of the Pade's comparisons and exponent steps (FP64 instructions are the
-// evaluation's cost on this GPU): |v| compared through its bit pattern, which orders like |v|;
-// ilogb and scalbn by the exponent field for normal numbers (exact), the library routines
-// otherwise.  Every decision and value is the same as with the FP64 forms.
-__device__ __forceinline__ uint64_t pd_abs_bits(double v) {
-  return (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-}
-// |v| as an integer key ordered like |v|; NaN -> 0 (loses every strict comparison, as in FP64)
-__device__ __forceinline__ uint64_t pd_key(double v) {
-  const uint64_t b = pd_abs_bits(v);
-  return b > 0x7FF0000000000000ull ? 0ull : b;
-}
-__device__ __forceinline__ int pd_ilogb(double v) {
-  const int e = (int)(((uint64_t)__double_as_longlong(v) >> 52) & 0x7FF);
-  return (e == 0 || e == 0x7FF) ? ilogb(v) : e - 1023;
-}
-__device__ __forceinline__ double pd_scalbn(double v, int n) {
-  const uint64_t b = (uint64_t)__double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0 || e == 0x7FF || e + n <= 0 || e + n >= 0x7FF) return scalbn(v, n);
-  return __longlong_as_double((long long)(b + ((uint64_t)(int64_t)n << 52)));
-}
-__device__ double pade_value(const double *a, int L, int M, int *status) {
-  const int n = L + M;
-  // growth rate of the series by the root test on its binary exponents,
-  // rounded up to an integer: rho = 2^k, so the rescaling below is exact
-  int first = 0;
-  while (first <= n && pd_abs_bits(a[first]) == 0) ++first;
-  int k = 0;
-  bool any = false;
-  for (int j = first + 1; j <= n; ++j) {
-    if (pd_abs_bits(a[j]) == 0) continue;
-    const int num = pd_ilogb(a[j]) - pd_ilogb(a[first]), den = j - first;
-    const int q = num > 0 ? (num + den - 1) / den : -((-num) / den);  // ceil(num / den)
-    k = any ? max(k, q) : q;
-    any = true;
+// Completion of one point from its resident per-chunk sums (rows S1, S2, S|W|, count of K+2
+// entries each; chunk slots pstride doubles apart): the first nch chunk sums added in chunk order
+// with compensation, a_n = S1_n / N and SE_n = sqrt((S2_n / N - a_n^2) / (N - 1)) (Sec. 2.4, Eq.
+// simplecase_discrete), the FP64 [L/M] Pade at eps = 1, HIGH_PRUNE when more than 1 % of the N
+// trees were pruned, and the bits `extra`.  All T threads of the block call it (it synchronises).
+__device__ __forceinline__ void complete_point(const double *part0, size_t pstride, uint32_t nch, double N, int K,
+                                               int L, int M, double *u, double *coef, double *se, int32_t *status,
+                                               int extra, int tid, int T) {
+  const int R = K + 2;
+  __shared__ double tot[4][kMaxK + 2];
+  __shared__ double a[kMaxK + 1];
+  for (int e = tid; e < 4 * R; e += T) {  // entry (stat, row) adds the point's chunk sums in chunk order
+    const double *pp = part0 + e;
+    double s = 0.0, c = 0.0;
+    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
+    tot[e / R][e % R] = s - c;
   }
-  const double rho = scalbn(1.0, k);
-  double c[kMaxK + 1];
-  for (int i = 0; i <= n; ++i) c[i] = pd_scalbn(a[i], -k * i);
-
-  int st = 0;
-  int Lc = L, Mc = M;
-  double beta[kMaxK + 1];
-  beta[0] = 1.0;
-  while (Mc > 0) {
-    double T[kMaxK][kMaxK + 1];  // row r: coefficients of beta_1..beta_Mc, then the right side
-    uint64_t bigk = 0;
-    for (int r = 0; r < Mc; ++r) {
-      for (int k = 0; k < Mc; ++k) {
-        const int idx = Lc + r - k;  // c_{L+i-j} with i = r+1, j = k+1
-        const double v = idx >= 0 ? c[idx] : 0.0;
-        T[r][k] = v;
-        bigk = max(bigk, pd_key(v));
-      }
-      T[r][Mc] = -c[Lc + r + 1];
-    }
-    bool ok = bigk > 0;
-    const uint64_t tiny = pd_key(1e-14 * __longlong_as_double((long long)bigk));
-    for (int k = 0; k < Mc && ok; ++k) {
-      int pr = k;
-      const uint64_t b0 = pd_abs_bits(T[k][k]);
-      if (b0 <= 0x7FF0000000000000ull) {  // a NaN pivot candidate keeps its row, as the FP64 scan does
-        uint64_t pvk = b0;
-        for (int r = k + 1; r < Mc; ++r) {
-          const uint64_t vk = pd_key(T[r][k]);
-          if (vk > pvk) {
-            pvk = vk;
-            pr = r;
-          }
-        }
-        if (pvk <= tiny) {
-          ok = false;
-          break;
-        }
-      }
-      if (pr != k) {
-        for (int j = k; j <= Mc; ++j) {
-          const double tmp = T[k][j];
-          T[k][j] = T[pr][j];
-          T[pr][j] = tmp;
-        }
-      }
-      const double inv = 1.0 / T[k][k];
-      for (int r = k + 1; r < Mc; ++r) {
-        const double m = T[r][k] * inv;
-        if (pd_abs_bits(m) != 0)
-          for (int j = k; j <= Mc; ++j) T[r][j] -= m * T[k][j];
-      }
-    }
-    if (ok) {
-      for (int r = Mc - 1; r >= 0; --r) {
-        double s = T[r][Mc];
-        for (int j = r + 1; j < Mc; ++j) s -= T[r][j] * beta[j + 1];
-        beta[r + 1] = s / T[r][r];
-      }
-      break;
-    }
-    st |= 1;  // PADE_SINGULAR
-    --Mc;
-    if (Lc > 0) --Lc;
+  __syncthreads();
+  if (tid <= K) {
+    const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
+    const double var = N > 1.0 ? (tot[1][tid] / N - an * an) / (N - 1.0) : 0.0;
+    a[tid] = an;
+    if (coef) coef[tid] = an;
+    if (se) se[tid] = var > 0.0 ? sqrt(var) : 0.0;
   }
-  // Q(rho) and P(rho) by Horner; numerator coefficients alpha_i = sum_j beta_j c_{i-j}
-  double Q = 0.0;
-  for (int j = Mc; j >= 0; --j) Q = Q * rho + beta[j];
-  double P = 0.0;
-  for (int i = Lc; i >= 0; --i) {
-    double al = 0.0;
-    const int jm = i < Mc ? i : Mc;
-    for (int j = 0; j <= jm; ++j) al += beta[j] * c[i - j];
-    P = P * rho + al;
+  __syncthreads();
+  if (tid == 0) {
+    const double pruned = tot[3][K + 1];
+    int st = 0;
+    const double v = pade_value(a, L, M, &st);
+    st |= extra;
+    if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
+    *u = v;
+    if (status) *status = st;
   }
-  if (fabs(Q) < 1e-8) st |= 2;  // PADE_POLE_NEAR
-  *status = st;
-  return P / Q;
 }
 
 // Binning (Sec. 2.4: trees of order n give the n-th series coefficient).
@@ -330,36 +225,30 @@ __global__ void __launch_bounds__(kFinThreads, 12) finalize_kernel(const Finaliz
   const uint32_t ntot = f.ntotal ? f.ntotal[pt] : f.ntrees[pt];
   if (cfirst + f.ntrees[pt] != ntot) return;  // more trees in a later launch: partials stay resident
   __threadfence();
-  __shared__ double tot[4][kMaxK + 2];
-  __shared__ double a[kMaxK + 1];
-  for (int e = tid; e < 4 * R; e += T) {  // entry (stat, row) adds the point's chunk sums in chunk order
-    const double *pp = f.part + (size_t)slot0 * pstride + e;
-    const uint32_t nch = ntot == 0u ? 1u : (ntot + kBinChunk - 1) / kBinChunk;
-    double s = 0.0, c = 0.0;
-    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
-    tot[e / R][e % R] = s - c;
-  }
-  __syncthreads();
-  const double N = (double)ntot;
+  const uint32_t nch = ntot == 0u ? 1u : (ntot + kBinChunk - 1) / kBinChunk;
   const size_t row = f.out_slot ? f.out_slot[pt] : (size_t)pt;
   const size_t ostride = f.out_stride ? f.out_stride : (size_t)(K + 1);
-  if (tid <= K) {
-    const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
-    const double var = N > 1.0 ? (tot[1][tid] / N - an * an) / (N - 1.0) : 0.0;
-    a[tid] = an;
-    if (f.coef) f.coef[row * ostride + tid] = an;
-    if (f.se) f.se[row * ostride + tid] = var > 0.0 ? sqrt(var) : 0.0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const double pruned = tot[3][K + 1];
-    int st = 0;
-    const double u = pade_value(a, f.L, f.M, &st);
-    if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
-    f.u[row] = u;
-    if (f.status) f.status[row] = st;
+  complete_point(f.part + (size_t)slot0 * pstride, pstride, nch, (double)ntot, K, f.L, f.M, f.u + row,
+                 f.coef ? f.coef + row * ostride : nullptr, f.se ? f.se + row * ostride : nullptr,
+                 f.status ? f.status + row : nullptr, 0, tid, T);
+}
 
-  }
+// Completion of points whose solve was stopped early (a cancelled server request): one block per
+// point, from the chunk sums of the trees binned so far, N = the trees those chunks hold; the
+// status carries `extra` (SERIES_PARTIAL).
+__global__ void __launch_bounds__(kFinThreads) complete_kernel(const CompleteParams c) {
+  const int i = blockIdx.x;
+  const size_t row = c.out_slot[i];
+  complete_point(c.part + (size_t)c.part_slot[i] * c.part_stride, c.part_stride, c.nchunks[i], (double)c.ntrees[i],
+                 c.K, c.L, c.M, c.u + row, c.coef ? c.coef + row * c.out_stride : nullptr,
+                 c.se ? c.se + row * c.out_stride : nullptr, c.status ? c.status + row : nullptr, c.extra_status,
+                 threadIdx.x, kFinThreads);
+}
+
+cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream) {
+  if (c.n <= 0) return cudaSuccess;
+  complete_kernel<<<(unsigned)c.n, kFinThreads, 0, stream>>>(c);
+  return cudaGetLastError();
 }
 
 __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, double *u, int32_t *status) {

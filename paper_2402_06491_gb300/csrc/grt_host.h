@@ -54,6 +54,7 @@ struct grt_ctx {
   grt::WalkConfig solve_cfg{};  // launch shape of grt_solve's walk (grt_set_solve_config)
   grt::DevBuf dx, dt, du, dcoef, dse, dstatus;
   grt::DevBuf pdd_scratch;  // spline weights, staging, plane data and subdomain vectors of the PDD stages
+  grt::DevBuf plain_part, plain_ticket;  // block partials and per-point tickets of grt_solve_plain
   int set_error(int code, const std::string &msg) {
     err = msg;
     return code;

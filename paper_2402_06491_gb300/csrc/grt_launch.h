@@ -63,6 +63,39 @@ cudaError_t launch_trees(bool fp64, int dim, int strategy, const WalkParams &p, 
                          uint32_t point, uint32_t first, uint32_t ntrees, int32_t *order, double *w, uint32_t *nodes,
                          uint64_t *hash, cudaStream_t stream);
 cudaError_t launch_finalize(bool fp64, const FinalizeParams &f, cudaStream_t stream);
+
+// Completion of points from the chunk sums binned so far (a stopped solve): one block per point.
+struct CompleteParams {
+  int n, K, L, M;
+  const double *part;        // resident chunk sums, slots part_stride doubles apart
+  size_t part_stride;
+  const uint32_t *part_slot; // [n] first chunk slot of each point
+  const uint32_t *nchunks;   // [n] chunks binned
+  const uint32_t *ntrees;    // [n] trees those chunks hold (N of the estimate)
+  const uint32_t *out_slot;  // [n] output row
+  size_t out_stride;         // doubles between coef / se rows
+  double *u, *coef, *se;
+  int32_t *status;
+  int extra_status;          // bits added to every point's status
+};
+cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream);
+
+// The plain FP64 path (grt_plain.cu): one launch per point.
+constexpr int kPlainThreads = 128;
+struct PlainPoint {
+  double x[3];             // the point (entries past dim unused)
+  double t;
+  uint32_t point;          // random-stream point index
+  uint32_t ntrees;
+  int K, L, M;
+  double *part;            // [blocks][3][K+2] block partials (S1, S2, SA rows; the pruned count in S1's row K+1)
+  uint32_t *ticket;        // zero before the launch
+  double *u;               // this point's outputs: u, coef [K+1] and se [K+1] (may be null), status (may be null)
+  double *coef, *se;
+  int32_t *status;
+};
+cudaError_t launch_plain(int dim, int strategy, const WalkParams &p, const PlainPoint &q, unsigned blocks,
+                         cudaStream_t stream);
 cudaError_t launch_pade(int n, int K, int L, int M, const double *coef, double *u, int32_t *status,
                         cudaStream_t stream);
 

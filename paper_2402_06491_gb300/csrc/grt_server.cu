@@ -12,7 +12,12 @@
 // are added in chunk order when the point completes, a point's result is the
 // same bits whether it was solved alone, in one launch, or over many steps.
 // Admission is by device memory: a request waits until its resident chunk
-// sums and result rows fit the budget.
+// sums and result rows fit the budget.  The groups of one step run on several
+// streams at once (disjoint regions of the step buffers), so the launches of
+// different requests overlap on the device.  A cancelled request stops taking
+// trees after the current step; each of its unfinished points is completed
+// from the chunks binned so far (N_done trees, a multiple of 8192) and marked
+// SERIES_PARTIAL -- the estimate of Sec. 2.4 over fewer independent trees.
 #include <algorithm>
 #include <cmath>
 #include <chrono>
@@ -24,6 +29,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "grt.h"
@@ -36,6 +42,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr size_t kPartStride = 4 * (GRT_MAX_K + 2);  // doubles per resident chunk slot
 constexpr size_t kOutStride = GRT_MAX_K + 1;         // doubles per coef / se row
+constexpr int kStreams = 4;                          // streams the groups of a step run on
 
 // First-fit allocator of row ranges in [0, capacity).
 class RowPool {
@@ -102,7 +109,8 @@ struct Request {
   uint64_t part_row = 0, part_rows = 0, out_row = 0;
   uint64_t remaining = 0;          // trees not yet walked
   int64_t points_left = 0;
-  bool admitted = false, finished = false;
+  bool admitted = false, finished = false, cancelled = false;
+  uint64_t shared_launches = 0, shared_steps = 0;  // launches / steps that also ran another request's trees
   int error = 0;
   std::string error_text;
   std::vector<double> u, coef, se;
@@ -126,9 +134,10 @@ struct grt_server {
   int num_sms = 0;
   uint64_t budget = 0, step_trees = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t streams[kStreams] = {};
   grt::DevBuf part_pool, out_u, out_coef, out_se, out_status;
   RowPool part_rows, out_rows;
-  grt::DevBuf rec_w, rec_o, meta, xbuf, work;
+  grt::DevBuf rec_w, rec_o, meta, xbuf, work, cmeta;
   size_t meta_points = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -140,7 +149,7 @@ struct grt_server {
   uint64_t next_id = 1;
   std::string err;
   int fatal = 0;
-  uint64_t steps = 0, trees_walked = 0, launches = 0;
+  uint64_t steps = 0, trees_walked = 0, launches = 0, shared_launches = 0, cancelled = 0;
 
   int set_error(int code, const std::string &m) {
     err = m;
@@ -148,6 +157,8 @@ struct grt_server {
   }
   void run();
   int run_step(std::vector<Unit> &units, std::string &why);
+  int complete_cancelled(const std::vector<Request *> &reqs, std::string &why);
+  void release_buffers();
 };
 
 namespace {
@@ -172,6 +183,18 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     return a->seed < b->seed;
   };
   std::stable_sort(units.begin(), units.end(), [&](const Unit &a, const Unit &b) { return key_less(a.r, b.r); });
+  // every group gets disjoint regions of the step buffers (points, records, work counters), so the
+  // groups run concurrently on the server's streams
+  const size_t u32n = (2 * meta_points + 1) * sizeof(uint32_t);  // entries of one per-point array
+  unsigned char *mb = meta.as<unsigned char>();
+  uint32_t *a_ntrees = reinterpret_cast<uint32_t *>(mb + 0 * u32n), *a_prefix = reinterpret_cast<uint32_t *>(mb + 1 * u32n),
+           *a_first = reinterpret_cast<uint32_t *>(mb + 2 * u32n), *a_pid = reinterpret_cast<uint32_t *>(mb + 3 * u32n),
+           *a_ntot = reinterpret_cast<uint32_t *>(mb + 4 * u32n), *a_pslot = reinterpret_cast<uint32_t *>(mb + 5 * u32n),
+           *a_oslot = reinterpret_cast<uint32_t *>(mb + 6 * u32n), *a_cpre = reinterpret_cast<uint32_t *>(mb + 7 * u32n);
+  unsigned long long *a_tpre = reinterpret_cast<unsigned long long *>(mb + 8 * u32n);
+  double *a_x = xbuf.as<double>(), *a_t = a_x + 2 * meta_points * GRT_MAX_DIM;
+  size_t pt_off = 0, rec_off = 0, work_off = 0;
+  int gidx = 0;
   size_t g0 = 0;
   while (g0 < units.size()) {
     size_t g1 = g0 + 1;
@@ -193,9 +216,15 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     m.x.resize(n * dim);
     m.t.resize(n);
     uint64_t items = 0, recs = 0, chunks = 0;
+    const Request *last = nullptr;
+    int distinct = 0;
     for (size_t k = 0; k < n; ++k) {
       const Unit &u = units[g0 + k];
       const Request &r = *u.r;
+      if (u.r != last) {  // units of one request are contiguous within the group
+        ++distinct;
+        last = u.r;
+      }
       m.ntrees[k] = u.cnt;
       m.prefix[k] = (uint32_t)items;
       m.tree_prefix[k] = recs;
@@ -214,22 +243,33 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     m.prefix[n] = (uint32_t)items;
     m.tree_prefix[n] = recs;
     m.chunk_prefix[n] = (uint32_t)chunks;
-    // device copies of the group's arrays (the buffers are sized at server creation)
-    if (n > meta_points) {
-      why = "step has more points than the server's step buffers hold";
+    if (distinct > 1) {  // this walk launch batches trees of several requests
+      ++shared_launches;
+      last = nullptr;
+      for (size_t k = g0; k < g1; ++k)
+        if (units[k].r != last) {
+          last = units[k].r;
+          ++units[k].r->shared_launches;
+        }
+    }
+    const size_t work_bytes = (64 + n * sizeof(uint32_t) + 63) & ~(size_t)63;
+    if (pt_off + n + 1 > 2 * meta_points + 1 || (rec_off + recs) * 8 > rec_w.cap ||
+        rec_off + recs > rec_o.cap || work_off + work_bytes > work.cap) {
+      why = "step larger than the server's step buffers";
       return GRT_EINVAL;
     }
-    unsigned char *mb = meta.as<unsigned char>();
-    const size_t u32n = (meta_points + 1) * sizeof(uint32_t);
-    uint32_t *d_ntrees = reinterpret_cast<uint32_t *>(mb + 0 * u32n), *d_prefix = reinterpret_cast<uint32_t *>(mb + 1 * u32n),
-             *d_first = reinterpret_cast<uint32_t *>(mb + 2 * u32n), *d_pid = reinterpret_cast<uint32_t *>(mb + 3 * u32n),
-             *d_ntot = reinterpret_cast<uint32_t *>(mb + 4 * u32n), *d_pslot = reinterpret_cast<uint32_t *>(mb + 5 * u32n),
-             *d_oslot = reinterpret_cast<uint32_t *>(mb + 6 * u32n), *d_cpre = reinterpret_cast<uint32_t *>(mb + 7 * u32n);
-    unsigned long long *d_tpre = reinterpret_cast<unsigned long long *>(mb + 8 * u32n);
-    double *d_x = xbuf.as<double>(), *d_t = d_x + meta_points * GRT_MAX_DIM;
+    cudaStream_t st = streams[gidx % kStreams];
+    uint32_t *d_ntrees = a_ntrees + pt_off, *d_prefix = a_prefix + pt_off, *d_first = a_first + pt_off,
+             *d_pid = a_pid + pt_off, *d_ntot = a_ntot + pt_off, *d_pslot = a_pslot + pt_off,
+             *d_oslot = a_oslot + pt_off, *d_cpre = a_cpre + pt_off;
+    unsigned long long *d_tpre = a_tpre + pt_off;
+    double *d_x = a_x + pt_off * GRT_MAX_DIM, *d_t = a_t + pt_off;
+    unsigned char *d_work = work.as<unsigned char>() + work_off;
+    unsigned char *d_recw = rec_w.as<unsigned char>() + rec_off * 8;  // 8 bytes per slot: FP32 or FP64 records
+    uint8_t *d_reco = rec_o.as<uint8_t>() + rec_off;
     cudaError_t e = cudaSuccess;
     auto cp = [&](void *dst, const void *src, size_t bytes) {
-      if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
     };
     cp(d_ntrees, m.ntrees.data(), n * 4);
     cp(d_prefix, m.prefix.data(), (n + 1) * 4);
@@ -242,7 +282,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     cp(d_tpre, m.tree_prefix.data(), (n + 1) * 8);
     cp(d_x, m.x.data(), n * dim * 8);
     cp(d_t, m.t.data(), n * 8);
-    if (e == cudaSuccess) e = cudaMemsetAsync(work.ptr, 0, 64 + n * sizeof(uint32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_work, 0, 64 + n * sizeof(uint32_t), st);
     if (e != cudaSuccess) {
       why = std::string("step copies: ") + cudaGetErrorString(e);
       return GRT_EDEVICE;
@@ -267,24 +307,24 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     w.n = (int)n;
     w.tile = grt::kTile;
     w.total_items = (uint32_t)items;
-    w.rec_w = rec_w.ptr;
-    w.rec_o = rec_o.as<uint8_t>();
-    w.counter = work.as<uint32_t>();
-    w.stats = reinterpret_cast<unsigned long long *>(work.as<unsigned char>() + 8);
+    w.rec_w = d_recw;
+    w.rec_o = d_reco;
+    w.counter = reinterpret_cast<uint32_t *>(d_work);
+    w.stats = reinterpret_cast<unsigned long long *>(d_work + 8);
     const bool fp64 = c->pb.precision == GRT_FP64;
     if (items > 0) {
-      e = grt::launch_walk(fp64, dim, c->pb.strategy, w, grt::WalkConfig{}, num_sms, stream);
+      e = grt::launch_walk(fp64, dim, c->pb.strategy, w, grt::WalkConfig{}, num_sms, st);
       ++launches;
     }
     grt::FinalizeParams f{};
-    f.rec_w = rec_w.ptr;
-    f.rec_o = rec_o.as<uint8_t>();
+    f.rec_w = d_recw;
+    f.rec_o = d_reco;
     f.tree_prefix = d_tpre;
     f.ntrees = d_ntrees;
     f.chunk_prefix = d_cpre;
     f.total_chunks = (uint32_t)chunks;
     f.part = part_pool.as<double>();
-    f.done = reinterpret_cast<uint32_t *>(work.as<unsigned char>() + 64);
+    f.done = reinterpret_cast<uint32_t *>(d_work + 64);
     f.tree_first = d_first;
     f.ntotal = d_ntot;
     f.part_slot = d_pslot;
@@ -300,18 +340,74 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     f.se = out_se.as<double>();
     f.status = out_status.as<int32_t>();
     f.stats = w.stats;
-    if (e == cudaSuccess) e = grt::launch_finalize(fp64, f, stream);
+    if (e == cudaSuccess) e = grt::launch_finalize(fp64, f, st);
     ++launches;
     if (e != cudaSuccess) {
       why = std::string("step launch: ") + cudaGetErrorString(e);
       return GRT_EDEVICE;
     }
+    pt_off += n + 1;
+    rec_off += recs;
+    work_off += work_bytes;
+    ++gidx;
     g0 = g1;
   }
-  const cudaError_t e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) {
-    why = std::string("step: ") + cudaGetErrorString(e);
-    return GRT_EDEVICE;
+  for (int k = 0; k < kStreams && k < std::max(gidx, 1); ++k) {
+    const cudaError_t e = cudaStreamSynchronize(streams[k]);
+    if (e != cudaSuccess) {
+      why = std::string("step: ") + cudaGetErrorString(e);
+      return GRT_EDEVICE;
+    }
+  }
+  return GRT_OK;
+}
+
+// Completion of the unfinished points of cancelled requests from the chunks binned so far.
+int grt_server::complete_cancelled(const std::vector<Request *> &reqs, std::string &why) {
+  // one completion launch per series shape (K, L, M); points of one request share it
+  std::map<std::tuple<int, int, int>, std::vector<std::pair<Request *, int64_t>>> by_shape;
+  for (Request *r : reqs)
+    for (int64_t i = 0; i < r->n; ++i)
+      if (!r->complete[i]) by_shape[std::make_tuple(r->K, r->L, r->M)].push_back({r, i});
+  for (auto &kv : by_shape) {
+    const auto &pts = kv.second;
+    const size_t n = pts.size();
+    std::vector<uint32_t> h((size_t)4 * n);  // part slot, chunks, trees, output row
+    for (size_t k = 0; k < n; ++k) {
+      const Request *r = pts[k].first;
+      const int64_t i = pts[k].second;
+      h[k] = r->part_slot[i];
+      h[n + k] = r->done[i] / grt::kBinChunk;  // an unfinished point's ranges end on chunk boundaries
+      h[2 * n + k] = r->done[i];
+      h[3 * n + k] = (uint32_t)(r->out_row + (uint64_t)i);
+    }
+    cudaError_t e = cmeta.ensure(h.size() * sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cmeta.ptr, h.data(), h.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, streams[0]);
+    grt::CompleteParams cp{};
+    cp.n = (int)n;
+    cp.K = std::get<0>(kv.first);
+    cp.L = std::get<1>(kv.first);
+    cp.M = std::get<2>(kv.first);
+    cp.part = part_pool.as<double>();
+    cp.part_stride = kPartStride;
+    cp.part_slot = cmeta.as<uint32_t>();
+    cp.nchunks = cp.part_slot + n;
+    cp.ntrees = cp.part_slot + 2 * n;
+    cp.out_slot = cp.part_slot + 3 * n;
+    cp.out_stride = kOutStride;
+    cp.u = out_u.as<double>();
+    cp.coef = out_coef.as<double>();
+    cp.se = out_se.as<double>();
+    cp.status = out_status.as<int32_t>();
+    cp.extra_status = GRT_STATUS_SERIES_PARTIAL;
+    if (e == cudaSuccess) e = grt::launch_complete(cp, streams[0]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(streams[0]);
+    ++launches;
+    if (e != cudaSuccess) {
+      why = std::string("completion of cancelled requests: ") + cudaGetErrorString(e);
+      return GRT_EDEVICE;
+    }
   }
   return GRT_OK;
 }
@@ -319,81 +415,20 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
 void grt_server::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lock(mu);
-  while (!stop) {
-    // admission: first come, first admitted, while the resident state fits the budget
-    while (!pending.empty()) {
-      Request *r = pending.front();
-      uint64_t prow = 0, orow = 0;
-      if (!part_rows.alloc(r->part_rows, &prow)) break;
-      if (!out_rows.alloc((uint64_t)r->n, &orow)) {
-        part_rows.release(prow, r->part_rows);
-        break;
-      }
-      r->part_row = prow;
-      r->out_row = orow;
-      uint64_t slot = prow;
-      for (int64_t i = 0; i < r->n; ++i) {
-        r->part_slot[i] = (uint32_t)slot;
-        slot += point_chunks(r->N[i]);
-      }
-      r->admitted = true;
-      pending.pop_front();
-      active.push_back(r);
+  auto fail_all = [&](int rc, const std::string &why) {
+    fatal = rc;
+    err = why;
+    for (Request *r : active) {
+      r->error = rc;
+      r->error_text = why;
+      r->finished = true;
+      r->t_finish = Clock::now();
     }
-    if (active.empty()) {
-      cv_work.wait(lock);
-      continue;
-    }
-    // the step's work: smallest remaining first; ranges start on chunk boundaries
-    std::vector<Request *> order(active);
-    std::stable_sort(order.begin(), order.end(), [](const Request *a, const Request *b) {
-      if (a->remaining != b->remaining) return a->remaining < b->remaining;
-      return a->id < b->id;
-    });
-    std::vector<Unit> units;
-    uint64_t budget_left = step_trees;
-    for (Request *r : order) {
-      for (int64_t i = 0; i < r->n && units.size() < meta_points; ++i) {
-        if (r->complete[i]) continue;
-        const uint32_t left = r->N[i] - r->done[i];
-        uint64_t take = std::min<uint64_t>(left, budget_left);
-        if (take < left) take -= take % grt::kBinChunk;  // a partial range ends on a chunk boundary
-        if (take == 0 && left > 0) continue;
-        units.push_back(Unit{r, i, r->done[i], (uint32_t)take});
-        budget_left -= take;
-        if (budget_left < grt::kBinChunk) budget_left = 0;
-      }
-      if (budget_left == 0 || units.size() >= meta_points) break;
-    }
-    lock.unlock();
-    std::string why;
-    const int rc = run_step(units, why);
-    lock.lock();
-    ++steps;
-    if (rc != GRT_OK) {
-      fatal = rc;
-      err = why;
-      for (Request *r : active) {
-        r->error = rc;
-        r->error_text = why;
-        r->finished = true;
-        r->t_finish = Clock::now();
-      }
-      active.clear();
-      cv_done.notify_all();
-      continue;
-    }
-    // bookkeeping; finished requests take their results off the device and free their rows
-    for (const Unit &u : units) {
-      Request *r = u.r;
-      r->done[u.i] += u.cnt;
-      r->remaining -= u.cnt;
-      trees_walked += u.cnt;
-      if (r->done[u.i] == r->N[u.i]) {
-        r->complete[u.i] = 1;
-        --r->points_left;
-      }
-    }
+    active.clear();
+    cv_done.notify_all();
+  };
+  // requests whose every point is done take their results off the device and free their rows
+  auto finish_done = [&]() {
     for (size_t k = 0; k < active.size();) {
       Request *r = active[k];
       if (r->points_left > 0) {
@@ -425,10 +460,130 @@ void grt_server::run() {
       active.erase(active.begin() + (ptrdiff_t)k);
     }
     cv_done.notify_all();
+  };
+  while (!stop) {
+    // admission: first come, first admitted, while the resident state fits the budget
+    while (!pending.empty()) {
+      Request *r = pending.front();
+      uint64_t prow = 0, orow = 0;
+      if (!part_rows.alloc(r->part_rows, &prow)) break;
+      if (!out_rows.alloc((uint64_t)r->n, &orow)) {
+        part_rows.release(prow, r->part_rows);
+        break;
+      }
+      r->part_row = prow;
+      r->out_row = orow;
+      uint64_t slot = prow;
+      for (int64_t i = 0; i < r->n; ++i) {
+        r->part_slot[i] = (uint32_t)slot;
+        slot += point_chunks(r->N[i]);
+      }
+      r->admitted = true;
+      pending.pop_front();
+      active.push_back(r);
+    }
+    // cancelled requests: their unfinished points are completed from the chunks binned so far
+    std::vector<Request *> canc;
+    for (Request *r : active)
+      if (r->cancelled && r->points_left > 0) canc.push_back(r);
+    if (!canc.empty()) {
+      lock.unlock();
+      std::string why;
+      const int rc = complete_cancelled(canc, why);
+      lock.lock();
+      if (rc != GRT_OK) {
+        fail_all(rc, why);
+        continue;
+      }
+      for (Request *r : canc) {
+        for (int64_t i = 0; i < r->n; ++i) r->complete[i] = 1;
+        r->points_left = 0;
+        ++cancelled;
+      }
+      finish_done();
+      continue;
+    }
+    if (active.empty()) {
+      cv_work.wait(lock);
+      continue;
+    }
+    // the step's work: smallest remaining first; ranges start on chunk boundaries
+    std::vector<Request *> order(active);
+    std::stable_sort(order.begin(), order.end(), [](const Request *a, const Request *b) {
+      if (a->remaining != b->remaining) return a->remaining < b->remaining;
+      return a->id < b->id;
+    });
+    std::vector<Unit> units;
+    uint64_t budget_left = step_trees;
+    for (Request *r : order) {
+      if (r->cancelled) continue;
+      for (int64_t i = 0; i < r->n && units.size() < meta_points; ++i) {
+        if (r->complete[i]) continue;
+        const uint32_t left = r->N[i] - r->done[i];
+        uint64_t take = std::min<uint64_t>(left, budget_left);
+        if (take < left) take -= take % grt::kBinChunk;  // a partial range ends on a chunk boundary
+        if (take == 0 && left > 0) continue;
+        units.push_back(Unit{r, i, r->done[i], (uint32_t)take});
+        budget_left -= take;
+        if (budget_left < grt::kBinChunk) budget_left = 0;
+      }
+      if (budget_left == 0 || units.size() >= meta_points) break;
+    }
+    if (units.empty()) {  // only cancelled requests are left: the next pass completes them
+      cv_work.wait_for(lock, std::chrono::milliseconds(1));
+      continue;
+    }
+    lock.unlock();
+    std::string why;
+    const int rc = run_step(units, why);
+    lock.lock();
+    ++steps;
+    if (rc != GRT_OK) {
+      fail_all(rc, why);
+      continue;
+    }
+    // bookkeeping
+    std::vector<Request *> in_step;
+    for (const Unit &u : units) {
+      Request *r = u.r;
+      if (in_step.empty() || in_step.back() != r) in_step.push_back(r);
+      r->done[u.i] += u.cnt;
+      r->remaining -= u.cnt;
+      trees_walked += u.cnt;
+      if (r->done[u.i] == r->N[u.i]) {
+        r->complete[u.i] = 1;
+        --r->points_left;
+      }
+    }
+    std::sort(in_step.begin(), in_step.end());
+    in_step.erase(std::unique(in_step.begin(), in_step.end()), in_step.end());
+    if (in_step.size() > 1)
+      for (Request *r : in_step) ++r->shared_steps;
+    finish_done();
   }
 }
 
 extern "C" {
+
+void grt_server::release_buffers() {
+  part_pool.release();
+  out_u.release();
+  out_status.release();
+  out_coef.release();
+  out_se.release();
+  rec_w.release();
+  rec_o.release();
+  meta.release();
+  xbuf.release();
+  work.release();
+  cmeta.release();
+  for (auto &st : streams)
+    if (st) {
+      cudaStreamDestroy(st);
+      st = nullptr;
+    }
+  stream = nullptr;
+}
 
 int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees, grt_server **out) {
   if (!out) return GRT_EINVAL;
@@ -443,7 +598,14 @@ int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees
   s->budget = mem_budget_bytes;
   s->step_trees = step_trees;
   s->meta_points = (size_t)std::min<uint64_t>(1ull << 20, std::max<uint64_t>(4096, step_trees / 256));
-  const size_t step_bytes = (size_t)step_trees * 9 + 64 * 1024 + s->meta_points * (9 * 4 + 8 + 4 * 8 + 4);
+  const size_t mp = s->meta_points;
+  // step buffers: records (8 + 1 bytes per tree slot, 4-aligned per point), per-point arrays of up
+  // to 2 mp + 1 entries (a group's arrays hold n + 1 entries), coordinates, work counters per group
+  const size_t meta_bytes = 10 * (2 * mp + 1) * sizeof(uint32_t);
+  const size_t xbuf_bytes = 2 * mp * (GRT_MAX_DIM + 1) * sizeof(double);
+  const size_t work_bytes = 132 * mp + 64;
+  const size_t rec_slots = (size_t)step_trees + 4 * mp + 64;
+  const size_t step_bytes = rec_slots * 9 + meta_bytes + xbuf_bytes + work_bytes + 64 * 1024;
   if (mem_budget_bytes < step_bytes + (1ull << 20)) {
     delete s;
     return GRT_EINVAL;  // the budget must hold the step buffers and some resident state
@@ -451,33 +613,26 @@ int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees
   const uint64_t resident = mem_budget_bytes - step_bytes;
   const uint64_t part_cap = (resident * 3 / 4) / (kPartStride * 8);
   const uint64_t out_cap = (resident / 4) / ((2 * kOutStride + 2) * 8);
-  cudaError_t e;
-  if ((e = cudaSetDevice(device)) != cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = s->part_pool.ensure(part_cap * kPartStride * 8)) != cudaSuccess ||
-      (e = s->out_u.ensure(out_cap * 8)) != cudaSuccess || (e = s->out_status.ensure(out_cap * 4)) != cudaSuccess ||
-      (e = s->out_coef.ensure(out_cap * kOutStride * 8)) != cudaSuccess ||
-      (e = s->out_se.ensure(out_cap * kOutStride * 8)) != cudaSuccess ||
-      (e = s->rec_w.ensure((size_t)step_trees * 8 + 4 * 8 * s->meta_points + 64)) != cudaSuccess ||
-      (e = s->rec_o.ensure((size_t)step_trees + 4 * s->meta_points + 64)) != cudaSuccess ||
-      (e = s->meta.ensure(9 * (s->meta_points + 1) * 4 + (s->meta_points + 1) * 8)) != cudaSuccess ||
-      (e = s->xbuf.ensure(s->meta_points * (GRT_MAX_DIM + 1) * 8)) != cudaSuccess ||
-      (e = s->work.ensure(64 + s->meta_points * 4)) != cudaSuccess) {
-    s->part_pool.release();
-    s->out_u.release();
-    s->out_status.release();
-    s->out_coef.release();
-    s->out_se.release();
-    s->rec_w.release();
-    s->rec_o.release();
-    s->meta.release();
-    s->xbuf.release();
-    s->work.release();
-    if (s->stream) cudaStreamDestroy(s->stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
+  for (int k = 0; k < kStreams && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = s->part_pool.ensure(part_cap * kPartStride * 8);
+  if (e == cudaSuccess) e = s->out_u.ensure(out_cap * 8);
+  if (e == cudaSuccess) e = s->out_status.ensure(out_cap * 4);
+  if (e == cudaSuccess) e = s->out_coef.ensure(out_cap * kOutStride * 8);
+  if (e == cudaSuccess) e = s->out_se.ensure(out_cap * kOutStride * 8);
+  if (e == cudaSuccess) e = s->rec_w.ensure(rec_slots * 8);
+  if (e == cudaSuccess) e = s->rec_o.ensure(rec_slots);
+  if (e == cudaSuccess) e = s->meta.ensure(meta_bytes);
+  if (e == cudaSuccess) e = s->xbuf.ensure(xbuf_bytes);
+  if (e == cudaSuccess) e = s->work.ensure(work_bytes);
+  if (e != cudaSuccess) {
+    s->release_buffers();
     delete s;
     return e == cudaErrorMemoryAllocation ? GRT_ENOMEM : GRT_EDEVICE;
   }
+  s->stream = s->streams[0];
   s->part_rows.init(part_cap);
   s->out_rows.init(out_cap);
   s->worker = std::thread([s]() { s->run(); });
@@ -495,17 +650,7 @@ void grt_server_destroy(grt_server *s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto &kv : s->reqs) delete kv.second;
   cudaSetDevice(s->device);
-  s->part_pool.release();
-  s->out_u.release();
-  s->out_status.release();
-  s->out_coef.release();
-  s->out_se.release();
-  s->rec_w.release();
-  s->rec_o.release();
-  s->meta.release();
-  s->xbuf.release();
-  s->work.release();
-  if (s->stream) cudaStreamDestroy(s->stream);
+  s->release_buffers();
   delete s;
 }
 
@@ -572,8 +717,40 @@ int grt_submit(grt_server *s, grt_ctx *c, int64_t n, const double *x, const doub
   return GRT_OK;
 }
 
-int grt_poll(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
-             int32_t *status_out, double *latency_s) {
+int grt_cancel(grt_server *s, uint64_t request_id) {
+  if (!s) return GRT_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return s->set_error(GRT_EINVAL, "unknown request id");
+    Request *r = it->second;
+    if (r->finished || r->cancelled) return GRT_OK;
+    r->cancelled = true;
+    if (!r->admitted) {  // still queued: no tree was walked, every point ends with N_done = 0
+      for (auto p = s->pending.begin(); p != s->pending.end(); ++p)
+        if (*p == r) {
+          s->pending.erase(p);
+          break;
+        }
+      const size_t n = (size_t)r->n, K1 = (size_t)r->K + 1;
+      r->u.assign(n, 0.0);
+      r->coef.assign(n * K1, 0.0);
+      r->se.assign(n * K1, 0.0);
+      // the Pade of an all-zero series: every pivot vanishes, [L/M] falls to [L-M/0] (singular when M > 0)
+      r->status.assign(n, GRT_STATUS_SERIES_PARTIAL | (r->M > 0 ? GRT_STATUS_PADE_SINGULAR : 0));
+      r->finished = true;
+      r->t_finish = Clock::now();
+      ++s->cancelled;
+      s->cv_done.notify_all();
+      return GRT_OK;
+    }
+  }
+  s->cv_work.notify_all();
+  return GRT_OK;
+}
+
+int grt_poll_ex(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
+                int32_t *status_out, uint64_t *ntrees_done, grt_request_info *info) {
   if (!s) return GRT_EINVAL;
   std::unique_lock<std::mutex> lock(s->mu);
   auto it = s->reqs.find(request_id);
@@ -588,23 +765,39 @@ int grt_poll(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, 
   }
   if (!r->finished) return GRT_EAGAIN;
   const int rc = r->error;
+  const size_t n = (size_t)r->n, K1 = (size_t)r->K + 1;
   if (rc == GRT_OK) {
-    const size_t n = (size_t)r->n, K1 = (size_t)r->K + 1;
     if (u_out && n) std::memcpy(u_out, r->u.data(), n * 8);
     if (status_out && n) std::memcpy(status_out, r->status.data(), n * 4);
     if (coef_out && n) std::memcpy(coef_out, r->coef.data(), n * K1 * 8);
     if (se_out && n) std::memcpy(se_out, r->se.data(), n * K1 * 8);
+    if (ntrees_done)
+      for (size_t i = 0; i < n; ++i) ntrees_done[i] = r->done[i];
   } else {
     s->err = r->error_text;
   }
-  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_finish - r->t_submit).count();
+  if (info) {
+    info->latency_s = std::chrono::duration<double>(r->t_finish - r->t_submit).count();
+    info->shared_launches = r->shared_launches;
+    info->shared_steps = r->shared_steps;
+    info->cancelled = r->cancelled ? 1 : 0;
+  }
   s->reqs.erase(it);
   delete r;
   return rc;
 }
 
+int grt_poll(grt_server *s, uint64_t request_id, int timeout_ms, double *u_out, double *coef_out, double *se_out,
+             int32_t *status_out, double *latency_s) {
+  grt_request_info info{};
+  const int rc = grt_poll_ex(s, request_id, timeout_ms, u_out, coef_out, se_out, status_out, nullptr, &info);
+  if (rc != GRT_EAGAIN && latency_s) *latency_s = info.latency_s;
+  return rc;
+}
+
 int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *launches, uint64_t *resident_bytes,
-                     uint64_t *pending_requests, uint64_t *active_requests) {
+                     uint64_t *pending_requests, uint64_t *active_requests, uint64_t *shared_launches,
+                     uint64_t *cancelled_requests) {
   if (!s) return GRT_EINVAL;
   std::lock_guard<std::mutex> lock(s->mu);
   if (steps) *steps = s->steps;
@@ -614,6 +807,8 @@ int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *
     *resident_bytes = s->part_rows.used() * kPartStride * 8 + s->out_rows.used() * (2 * kOutStride + 2) * 8;
   if (pending_requests) *pending_requests = s->pending.size();
   if (active_requests) *active_requests = s->active.size();
+  if (shared_launches) *shared_launches = s->shared_launches;
+  if (cancelled_requests) *cancelled_requests = s->cancelled;
   return GRT_OK;
 }
 

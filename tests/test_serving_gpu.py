@@ -5,10 +5,12 @@ same points (same stream indices and seed) -- alone or in any mix of concurrent
 requests, and however the scheduler split its trees over steps.
 """
 import threading
+import time
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -61,6 +63,8 @@ def test_results_equal_one_shot_solves_in_a_concurrent_mix(grt):
     results = [grt.grt_poll(server, rid, -1) for rid in ids]
     stats = grt.grt_server_stats(server)
     assert stats["steps"] > 5 and stats["active"] == 0 and stats["pending"] == 0
+    from test_parity_gpu import _assert_fp32_parity
+
     for s, r in zip(specs, results):
         ref = grt.grt_solve(ctxs[s["name"]], s["x"], s["t"], s["ntrees"], s["K"], s["L"], s["M"], s["seed"],
                             s["point_base"])
@@ -69,6 +73,17 @@ def test_results_equal_one_shot_solves_in_a_concurrent_mix(grt):
         assert np.array_equal(r["status"], ref["status"]), s["name"]
         assert np.array_equal(r["u"], ref["u"]) or np.allclose(r["u"], ref["u"], equal_nan=True, rtol=0, atol=0)
         assert r["latency_s"] >= 0.0
+        # and against the FP64 oracle on the same streams (two points of every request)
+        for i in range(min(2, len(s["t"]))):
+            o = oracle.solve(s["problem"], s["x"][i:i + 1], s["t"][i:i + 1], s["ntrees"][i:i + 1], s["K"], s["L"],
+                             s["M"], s["seed"], point_base=s["point_base"] + i)
+            gi = {k: r[k][i:i + 1] for k in ("u", "coef", "status")}
+            if s["problem"]["precision"] == "fp64":
+                assert np.allclose(gi["coef"], o["coef"], rtol=1e-12, atol=1e-15), s["name"]
+            else:
+                ctol = 1.5e-4 if s["name"] == "pdd_3d" else 3e-5
+                blow = np.array([s["name"] == "uneven_2d" and s["t"][i] >= 0.5])
+                _assert_fp32_parity(gi, o, s["ntrees"][i:i + 1], ctol=ctol, L=s["L"], M=s["M"], unpinned=blow)
     server.close()
     for c in ctxs.values():
         c.close()
@@ -80,7 +95,8 @@ def test_admission_waits_for_memory(grt):
     # resident part of the budget: 1 MB = ~1365 chunk rows of 8192 trees; each request below
     # needs 20 points x 20 chunks = 400 rows, so at most three are admitted at a time
     step = 1 << 16
-    budget = step * 9 + 64 * 1024 + 4096 * 80 + (1 << 20)
+    P = 4096
+    budget = 9 * (step + 4 * P + 64) + 312 * P + 66 * 1024 + (1 << 20)
     server = grt.grt_server_create(0, mem_budget_bytes=budget, step_trees=step)
     nt = np.full(20, 20 * 8192, np.uint64)
     ids = []
@@ -122,4 +138,85 @@ def test_errors_and_empty_requests(grt):
     rid = grt.grt_submit(server, ctx, np.zeros((3, 2)), [0.5, 1.0, 0.25], [20000, 1, 0], 10, 5, 5, 7)
     assert grt.grt_poll(server, rid, -1)["u"].shape == (3,)
     server.close()
+    ctx.close()
+
+
+def test_requests_that_arrive_while_another_runs_share_its_launches(grt):
+    """A request submitted while another of the same problem, series shape and seed is on the GPU joins
+    the running request's walk launches (its points are batched into the same launch); one with another
+    seed runs in the same steps, in a launch of its own on another stream.  Each result is still the
+    one-shot solve's, bit for bit."""
+    wl = workloads.workload_sin_2d()
+    ctx = grt.grt_create(wl["problem"], 0)
+    server = grt.grt_server_create(0, mem_budget_bytes=512 << 20, step_trees=1 << 16)
+    K, L, M = wl["K"], wl["L"], wl["M"]
+    big = grt.grt_submit(server, ctx, wl["x"][:16], wl["t"][:16], np.full(16, 200_000, np.uint64), K, L, M, 1, 0)
+    t0 = time.time()
+    while grt.grt_server_stats(server)["steps"] < 2 and time.time() - t0 < 30:
+        time.sleep(0.001)
+    # small requests: the scheduler takes smallest remaining work first, so both fit in the next step
+    # beside a range of the big request
+    same = grt.grt_submit(server, ctx, wl["x"][16:20], wl["t"][16:20], np.full(4, 3000, np.uint64), K, L, M, 1, 16)
+    other = grt.grt_submit(server, ctx, wl["x"][20:24], wl["t"][20:24], np.full(4, 3000, np.uint64), K, L, M, 2, 20)
+    rb, rs, ro = (grt.grt_poll_ex(server, rid, -1) for rid in (big, same, other))
+    stats = grt.grt_server_stats(server)
+    assert rs["shared_launches"] >= 1 and rb["shared_launches"] >= 1 and stats["shared_launches"] >= 1
+    assert ro["shared_steps"] >= 1 and rb["shared_steps"] >= 1
+    for r, sl, seed in ((rb, slice(0, 16), 1), (rs, slice(16, 20), 1), (ro, slice(20, 24), 2)):
+        n = sl.stop - sl.start
+        ref = grt.grt_solve(ctx, wl["x"][sl], wl["t"][sl], r["ntrees_done"], K, L, M, seed, sl.start)
+        assert np.array_equal(r["coef"], ref["coef"]) and np.array_equal(r["u"], ref["u"])
+        assert not r["cancelled"] and np.all(r["status"] & grt.STATUS_SERIES_PARTIAL == 0) and n == len(r["u"])
+    server.close()
+    ctx.close()
+
+
+def test_cancelled_request_ends_with_the_trees_binned_so_far(grt):
+    """grt_cancel mid-request: every point that had not received all its trees ends with N_done (a
+    multiple of 8192, below N) and SERIES_PARTIAL; its coefficients, standard errors and Pade value are
+    grt_solve's with N = N_done, bit for bit, and agree with the FP64 oracle over those N_done trees.
+    A request still waiting for admission ends with N_done = 0."""
+    wl = workloads.workload_sin_2d()
+    ctx = grt.grt_create(wl["problem"], 0)
+    K, L, M = wl["K"], wl["L"], wl["M"]
+    step = 1 << 16
+    P = 4096
+    budget = 9 * (step + 4 * P + 64) + 312 * P + 66 * 1024 + (1 << 20)  # ~1558 resident chunk rows
+    server = grt.grt_server_create(0, mem_budget_bytes=budget, step_trees=step)
+    nt = np.array([8 * 8192 + 5, 300_000, 1000, 500_000, 2 * 8192, 777_777], np.uint64)
+    x, t = wl["x"][100:106], wl["t"][100:106]
+    rid = grt.grt_submit(server, ctx, x, t, nt, K, L, M, 9, 100)
+    # a second request needing more resident rows than are left waits for admission
+    waiting = grt.grt_submit(server, ctx, wl["x"][:2], wl["t"][:2], np.full(2, 700 * 8192, np.uint64), K, L, M, 9, 0)
+    t0 = time.time()
+    while grt.grt_server_stats(server)["steps"] < 4 and time.time() - t0 < 30:
+        time.sleep(0.0005)
+    grt.grt_cancel(server, waiting)
+    grt.grt_cancel(server, rid)
+    r = grt.grt_poll_ex(server, rid, -1)
+    w = grt.grt_poll_ex(server, waiting, -1)
+    stats = grt.grt_server_stats(server)
+    server.close()
+    assert r["cancelled"] and w["cancelled"] and stats["cancelled"] == 2
+    nd = r["ntrees_done"]
+    partial = nd < nt
+    assert partial.any() and np.all(nd <= nt)
+    assert np.all(nd[partial] % 8192 == 0)
+    assert np.all((r["status"] & grt.STATUS_SERIES_PARTIAL != 0) == partial)
+    ref = grt.grt_solve(ctx, x, t, nd, K, L, M, 9, 100)
+    assert np.array_equal(r["coef"], ref["coef"]) and np.array_equal(r["se"], ref["se"])
+    assert np.array_equal(r["u"], ref["u"], equal_nan=True)
+    assert np.array_equal(r["status"] & ~grt.STATUS_SERIES_PARTIAL, ref["status"])
+    i = int(np.argmax(partial & (nd > 0))) if np.any(partial & (nd > 0)) else None
+    if i is not None:
+        from test_parity_gpu import _assert_fp32_parity
+
+        o = oracle.solve(wl["problem"], x[i:i + 1], t[i:i + 1], nd[i:i + 1], K, L, M, 9, point_base=100 + i)
+        gi = {k: r[k][i:i + 1] for k in ("u", "coef")}
+        gi["status"] = r["status"][i:i + 1] & ~grt.STATUS_SERIES_PARTIAL
+        _assert_fp32_parity(gi, o, nd[i:i + 1], L=L, M=M)
+    assert np.all(w["ntrees_done"] == 0) and np.all(w["u"] == 0.0) and np.all(w["coef"] == 0.0)
+    assert np.all(w["status"] & grt.STATUS_SERIES_PARTIAL)
+    zero = grt.grt_solve(ctx, wl["x"][:2], wl["t"][:2], np.zeros(2, np.uint64), K, L, M, 9, 0)
+    assert np.array_equal(w["status"] & ~grt.STATUS_SERIES_PARTIAL, zero["status"])
     ctx.close()

@@ -121,3 +121,78 @@ def test_pdd_subdomains_shard_over_two_gloo_ranks(tmp_path):
     planes[:, ::6] = True
     combined = np.where(planes, parts[0], parts[0] + parts[1])
     assert np.array_equal(combined, full)
+
+
+BATCH = 1500
+
+
+def _fault_rank_main(rank, world, port, out_dir):
+    """Trees of each point cut into batches of BATCH, batch b on rank b % world; rank 1 loses its batch 1
+    (an exception on the host: the batch's sums never reach the exchange).  Every rank sends, per point
+    and batch, the order sums of its completed batches and the trees they hold; the dropped batch
+    contributes nothing, and the trees it would have held are not counted."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    wl = workloads.subsample(workloads.workload_sin_2d(), 3, ntrees=6000)
+    K, n = wl["K"], wl["x"].shape[0]
+    nb = (6000 + BATCH - 1) // BATCH
+    sums = torch.zeros((n, nb, K + 3), dtype=torch.float64)  # S1 per kept order, pruned count, trees
+    for p in range(n):
+        for b in range(rank, nb, world):
+            rec = oracle.trees(wl["problem"], wl["x"][p], float(wl["t"][p]), p, b * BATCH, BATCH, K, wl["seed"])
+            try:
+                if rank == 1 and b == 1:
+                    np.save(os.path.join(out_dir, f"lost_{p}.npy"), rec["w"])  # what the rank had computed
+                    raise RuntimeError("rank 1 lost batch 1")
+                for o in range(K + 1):
+                    sums[p, b, o] = float(np.sum(rec["w"][rec["order"] == o]))
+                sums[p, b, K + 1] = float(np.sum(rec["order"] > K))
+                sums[p, b, K + 2] = BATCH
+            except RuntimeError:
+                pass
+    dist.all_reduce(sums)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "sums.npy"), sums.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_dropped_tree_batches_leave_an_estimate_over_the_trees_done(tmp_path):
+    """Fault tolerance from independent samples (Sec. 3): when a rank loses a batch of trees, the
+    combined a_n = S1_n / N_done is the estimate over exactly the trees that were walked (checked
+    against the oracle's records of those trees), and the lost batch re-run on another rank gives the
+    same tree weights bit for bit (the streams are keyed by point, tree and node label)."""
+    pytest.importorskip("torch")
+    import socket
+
+    import torch.multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_fault_rank_main, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
+    sums = np.load(tmp_path / "sums.npy")
+    wl = workloads.subsample(workloads.workload_sin_2d(), 3, ntrees=6000)
+    K = wl["K"]
+    for p in range(sums.shape[0]):
+        n_done = sums[p, :, K + 2].sum()
+        assert n_done == 6000 - BATCH
+        a = sums[p, :, :K + 1].sum(axis=0) / n_done
+        kept = [b for b in range(sums.shape[1]) if b != 1]
+        rec = [oracle.trees(wl["problem"], wl["x"][p], float(wl["t"][p]), p, b * BATCH, BATCH, K, wl["seed"])
+               for b in kept]
+        w = np.concatenate([r["w"] for r in rec])
+        order = np.concatenate([r["order"] for r in rec])
+        expect = np.array([w[order == o].sum() for o in range(K + 1)]) / n_done
+        assert np.allclose(a, expect, rtol=1e-13, atol=1e-15)
+        again = oracle.trees(wl["problem"], wl["x"][p], float(wl["t"][p]), p, BATCH, BATCH, K, wl["seed"])
+        assert np.array_equal(again["w"], np.load(tmp_path / f"lost_{p}.npy"))
