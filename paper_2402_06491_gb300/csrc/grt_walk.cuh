@@ -32,12 +32,16 @@
 namespace grt {
 
 // Stack of pending frames, one per split with children still to walk:
-// (y[DIM], tau, child label base lo/hi, (k << 8) | next digit).  FP32 walks
-// keep a frame as two vectors laid out [level][lane] -- (y0, y1, tau, lo) and
-// (hi, nk) for d <= 2, (y0, y1, y2, tau) and (lo, hi, nk, -) for d = 3 -- so a
-// push or a pop is one 16-byte and one 8- or 16-byte shared access per lane,
-// conflict-free across the warp whatever the lanes' depths.  FP64 walks lay
-// the fields out field-major [field][level][lane].
+// (y[DIM], tau, meta), meta = (tree depth F of the split node << 16) |
+// (k << 8) | next digit.  The children's labels are not stored: node labels
+// are paths (child j of label id is 16 id + j + 1), so the split node's label
+// is the current label's first F hex digits, and its next child's label that
+// prefix followed by the digit.  FP32 walks keep a frame as one vector laid
+// out [level][lane] -- (y0, y1, tau, meta) for d <= 2; (y0, y1, y2, tau) plus
+// a 32-bit meta array for d = 3 -- so a push or a pop is one 16-byte (and for
+// d = 3 one 4-byte) shared access per lane, conflict-free across the warp
+// whatever the lanes' depths.  FP64 walks lay the fields out field-major
+// [field][level][lane].
 // SLEV = 0 keeps every level (K of them) in shared memory; SLEV > 0 keeps the
 // top SLEV levels there and deeper ones (rare: a frame is pushed only for
 // splits of arity >= 2) in per-thread local memory, for more resident warps.
@@ -47,7 +51,7 @@ __host__ __device__ inline int smem_levels(int K, int slev) {
 }
 
 template <typename Real, int DIM> __host__ __device__ constexpr size_t frame_bytes() {
-  return sizeof(Real) == 4 ? (DIM <= 2 ? 24 : 32) : (DIM + 1) * sizeof(Real) + 3 * sizeof(uint32_t);
+  return sizeof(Real) == 4 ? (DIM <= 2 ? 16 : 20) : (DIM + 1) * sizeof(Real) + sizeof(uint32_t);
 }
 
 template <typename Real, int DIM>
@@ -93,15 +97,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
   unsigned char *wb = smem + (size_t)warp * warp_stack_bytes<Real, DIM>(K, SLEV);
   constexpr int LL = SLEV > 0 ? kMaxK : 1;  // local-memory levels (unused when SLEV = 0)
   Real ly[LL][DIM], ltau[LL];
-  uint32_t llo[LL], lhi[LL], lnk[LL];
+  uint32_t lnk[LL];
   Real *stk_y = reinterpret_cast<Real *>(wb);             // [DIM][lv][32]
   Real *stk_tau = stk_y + (size_t)DIM * lv * 32;          // [lv][32]
-  uint32_t *stk_lo = reinterpret_cast<uint32_t *>(stk_tau + (size_t)lv * 32);
-  uint32_t *stk_hi = stk_lo + lv * 32;
-  uint32_t *stk_nk = stk_hi + lv * 32;
+  uint32_t *stk_nk = reinterpret_cast<uint32_t *>(stk_tau + (size_t)lv * 32);
   constexpr bool kVec = sizeof(Real) == 4;                 // FP32: vector frames
   float4 *fr_a = reinterpret_cast<float4 *>(wb);           // [lv][32]
-  unsigned char *fr_b = wb + (size_t)lv * 32 * sizeof(float4);  // [lv][32] of uint2 (d <= 2) or uint4 (d = 3)
+  uint32_t *fr_m = reinterpret_cast<uint32_t *>(wb + (size_t)lv * 32 * sizeof(float4));  // d = 3: [lv][32] meta
   const unsigned lt_mask = (1u << lane) - 1u;
 
   // warp-uniform: the chunk trees are handed out from
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
   // lane: the current node (position, remaining time, label) and the running tree
   Real x[DIM], tau = Real(0), W = Real(1);
   uint32_t id_lo = 0, id_hi = 0;
-  int Ne = 0, depth = 0;
+  int Ne = 0, depth = 0;  // splits so far; pending frames
+  uint32_t tdep = 0;      // tree depth of the current node (root 0)
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     base[i] = Real(0);
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
     id_hi = 0;
     Ne = 0;
     depth = 0;
+    tdep = 0;
     active = true;
   };
 
@@ -212,34 +216,29 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
     const int k = (split && !pruned) ? s_arity[o.cat] : 0;
     const bool down = k > 0;
     if (k > 1) {  // remember the remaining children 2 .. k: labels 16 id + 2 .. 16 id + k
-      const uint32_t clo = id_lo << 4, chi = __funnelshift_l(id_lo, id_hi, 4), cnk = ((uint32_t)k << 8) | 2u;
+      const uint32_t meta = (tdep << 16) | ((uint32_t)k << 8) | 2u;
       if (SLEV == 0 || depth < lv) {
         const int at = depth * 32 + lane;
         if constexpr (kVec) {
           if constexpr (DIM <= 2) {
             fr_a[at] = make_float4((float)o.y[0], DIM > 1 ? (float)o.y[DIM - 1] : 0.0f, (float)o.tau_c,
-                                   __uint_as_float(clo));
-            reinterpret_cast<uint2 *>(fr_b)[at] = make_uint2(chi, cnk);
+                                   __uint_as_float(meta));
           } else {
             fr_a[at] = make_float4((float)o.y[0], (float)o.y[1], (float)o.y[DIM - 1], (float)o.tau_c);
-            reinterpret_cast<uint4 *>(fr_b)[at] = make_uint4(clo, chi, cnk, 0u);
+            fr_m[at] = meta;
           }
         } else {
 #pragma unroll
           for (int i = 0; i < DIM; ++i) stk_y[(size_t)i * lv * 32 + at] = o.y[i];
           stk_tau[at] = o.tau_c;
-          stk_lo[at] = clo;
-          stk_hi[at] = chi;
-          stk_nk[at] = cnk;
+          stk_nk[at] = meta;
         }
       } else {
         const int at = depth - lv;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) ly[at][i] = o.y[i];
         ltau[at] = o.tau_c;
-        llo[at] = clo;
-        lhi[at] = chi;
-        lnk[at] = cnk;
+        lnk[at] = meta;
       }
       ++depth;
     }
@@ -250,42 +249,35 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
       tau = o.tau_c;
       id_hi = __funnelshift_l(id_lo, id_hi, 4);
       id_lo = (id_lo << 4) | 1u;
+      ++tdep;
     }
     if (up) {  // the next child of the frame on top; a frame whose last child this is is popped
       // (its digit is still advanced: the slot is free, and a push overwrites all of it)
       const int lvl = depth - 1;
-      uint32_t nk, clo;
+      uint32_t nk;
       if (SLEV == 0 || lvl < lv) {
         const int at = lvl * 32 + lane;
         if constexpr (kVec) {
           const float4 a = fr_a[at];
           if constexpr (DIM <= 2) {
-            const uint2 b = reinterpret_cast<const uint2 *>(fr_b)[at];
             x[0] = (Real)a.x;
             if (DIM > 1) x[DIM - 1] = (Real)a.y;
             tau = (Real)a.z;
-            clo = __float_as_uint(a.w);
-            id_hi = b.x;
-            nk = b.y;
-            reinterpret_cast<uint32_t *>(fr_b)[2 * at + 1] = nk + 1u;
+            nk = __float_as_uint(a.w);
+            reinterpret_cast<uint32_t *>(fr_a)[4 * at + 3] = nk + 1u;
           } else {
-            const uint4 b = reinterpret_cast<const uint4 *>(fr_b)[at];
             x[0] = (Real)a.x;
             x[1] = (Real)a.y;
             x[DIM - 1] = (Real)a.z;
             tau = (Real)a.w;
-            clo = b.x;
-            id_hi = b.y;
-            nk = b.z;
-            reinterpret_cast<uint32_t *>(fr_b)[4 * at + 2] = nk + 1u;
+            nk = fr_m[at];
+            fr_m[at] = nk + 1u;
           }
         } else {
 #pragma unroll
           for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
           tau = stk_tau[at];
           nk = stk_nk[at];
-          clo = stk_lo[at];
-          id_hi = stk_hi[at];
           stk_nk[at] = nk + 1u;
         }
       } else {
@@ -294,13 +286,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
         for (int i = 0; i < DIM; ++i) x[i] = ly[at][i];
         tau = ltau[at];
         nk = lnk[at];
-        clo = llo[at];
-        id_hi = lhi[at];
         lnk[at] = nk + 1u;
       }
-      const uint32_t nd = nk & 0xFFu;
-      id_lo = clo | nd;
-      if (nd == (nk >> 8)) --depth;
+      // the child's label: the split node's label (the current label without its last
+      // tdep - F digits) followed by the child's digit
+      const uint32_t nd = nk & 0xFFu, F = nk >> 16;
+      const uint32_t sh = 4u * (tdep - F);  // 4 .. 64
+      const uint64_t id = ((uint64_t)id_hi << 32) | id_lo;
+      const uint64_t idF = sh >= 64u ? 0ull : (id >> sh);
+      id_lo = ((uint32_t)idF << 4) | nd;
+      id_hi = (uint32_t)(idF >> 28);
+      tdep = F + 1u;
+      if (nd == ((nk >> 8) & 0xFFu)) --depth;
     }
     if (!down && !up) {  // leaf with nothing pending, or pruned
       reinterpret_cast<Real *>(p.rec_w)[rec] = pruned ? Real(0) : W;
