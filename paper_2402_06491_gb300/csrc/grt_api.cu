@@ -364,7 +364,7 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   p->total_items = (uint32_t)items;
   p->total_trees = trees;
   p->host_ntrees.assign(ntrees, ntrees + n);
-  p->launches = items > 0 ? 1 + (int)(p->group_pt.size() - 1) : 1;
+  p->launches = (items > 0 ? (int)(p->group_pt.size() - 1) : 0) + 2;  // walk launch(es), binning, completion
   return GRT_OK;
 }
 
@@ -415,17 +415,24 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   f.chunk_prefix = p->chunk_prefix.as<uint32_t>();
   f.total_chunks = p->total_chunks;
   f.part = p->part.as<double>();
-  f.done = reinterpret_cast<uint32_t *>(p->work.as<unsigned char>() + 64);
   f.n = (int)p->n;
   f.K = p->K;
-  f.L = p->L;
-  f.M = p->M;
-  f.u = d_u;
-  f.coef = d_coef;
-  f.se = d_se;
-  f.status = d_status;
   f.stats = w.stats;
   GRT_CUDA(c, grt::launch_finalize(fp64, f, stream));
+  // each point's chunk sums -> a_n, SE_n, Pade
+  grt::CompleteParams cp{};
+  cp.n = (int)p->n;
+  cp.K = p->K;
+  cp.L = p->L;
+  cp.M = p->M;
+  cp.part = p->part.as<double>();
+  cp.chunk_prefix = p->chunk_prefix.as<uint32_t>();
+  cp.ntrees = p->ntrees.as<uint32_t>();
+  cp.u = d_u;
+  cp.coef = d_coef;
+  cp.se = d_se;
+  cp.status = d_status;
+  GRT_CUDA(c, grt::launch_complete(cp, stream));
   if (p->timing) GRT_CUDA(c, cudaEventRecord(p->ev[2], stream));
   p->timed_last = p->timing;
   p->last_stream = stream;
@@ -1066,16 +1073,22 @@ extern "C" int grt_solve_noalloc(grt_ctx *c, int64_t n, const double *d_x, const
   f.chunk_prefix = reinterpret_cast<const uint32_t *>(base + kNaChunkPrefix);
   f.total_chunks = (uint32_t)chunks;
   f.part = reinterpret_cast<double *>(base + kNaPart);
-  f.done = reinterpret_cast<uint32_t *>(base + kNaWork + 64);
   f.n = (int)n;
   f.K = K;
-  f.L = L;
-  f.M = M;
-  f.u = d_u;
-  f.coef = d_coef;
-  f.se = d_se;
-  f.status = d_status;
   f.stats = w.stats;
   GRT_CUDA(c, grt::launch_finalize(fp64, f, stream));
+  grt::CompleteParams cp{};
+  cp.n = (int)n;
+  cp.K = K;
+  cp.L = L;
+  cp.M = M;
+  cp.part = f.part;
+  cp.chunk_prefix = f.chunk_prefix;
+  cp.ntrees = f.ntrees;
+  cp.u = d_u;
+  cp.coef = d_coef;
+  cp.se = d_se;
+  cp.status = d_status;
+  GRT_CUDA(c, grt::launch_complete(cp, stream));
   return GRT_OK;
 }

@@ -57,37 +57,42 @@ __device__ __forceinline__ void complete_point(const double *part0, size_t pstri
     if (se) se[tid] = var > 0.0 ? sqrt(var) : 0.0;
   }
   __syncthreads();
-  if (tid == 0) {
-    const double pruned = tot[3][K + 1];
+  if (tid < 32) {  // the first warp evaluates the Pade together
     int st = 0;
-    const double v = pade_value(a, L, M, &st);
-    st |= extra;
-    if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
-    *u = v;
-    if (status) *status = st;
+    const double v = pade_value_warp(a, L, M, &st, tid);
+    if (tid == 0) {
+      const double pruned = tot[3][K + 1];
+      st |= extra;
+      if (N > 0.0 && pruned > 0.01 * N) st |= 8;  // HIGH_PRUNE
+      *u = v;
+      if (status) *status = st;
+    }
   }
 }
+
+// Shape of the binning kernel: threads per block (one block per 8192-record chunk), record groups
+// each thread loads before binning them, and the minimum resident blocks in its launch bounds.
+constexpr int kBinThreads = 64;
+constexpr int kBinGroups = 4;
+constexpr int kFinMinBlocks = 16;
 
 // Binning (Sec. 2.4: trees of order n give the n-th series coefficient).
 // One block per chunk of kBinChunk consecutive tree records of one point.
 // Thread j bins record groups 4j .. 4j+3, 4(j+T) .. 4(j+T)+3, ... of the chunk
 // (T = kFinThreads) into its own shared-memory column of per-order sums (S1
 // with Kahan compensation, S2, S|W|, count); the columns are added in a fixed order and
-// the chunk's sums written to `part`.  The last block to finish a point
-// (fence + ticket, nobody waits) adds the point's chunk sums in chunk order,
-// forms a_n and SE_n and runs the FP64 Pade.  Every result depends only on
-// the records, not on block scheduling.
-template <typename Acc>
-// __launch_bounds__(threads, 12): the hint lets ptxas keep the per-point completion's state in
-// registers (77; 48 with 60 bytes of spills without it) at 12 resident blocks per SM: 141 -> 128 us
-__global__ void __launch_bounds__(kFinThreads, 12) finalize_kernel(const FinalizeParams f) {
+// the chunk's sums written to `part`.  A second kernel (complete_kernel, one
+// block per point) then adds each point's chunk sums in chunk order, forms a_n
+// and SE_n and runs the FP64 Pade: the binning blocks need few registers and
+// stay many per SM.  Every result depends only on the records, not on block
+// scheduling.
+template <typename Acc, int T, int G>
+__global__ void __launch_bounds__(T, kFinMinBlocks) finalize_kernel(const FinalizeParams f) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int T = kFinThreads;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = f.K, R = K + 2;  // rows: orders 0..K and the pruned trees
   const uint32_t chunk = blockIdx.x;
   __shared__ int s_pt;
-  __shared__ bool s_last;
   if (warp == 0) {  // point owning this chunk: largest p with chunk_prefix[p] <= chunk (32-way search)
     int lo = 0, hi = f.n;
     while (hi - lo > 1) {
@@ -136,29 +141,28 @@ __global__ void __launch_bounds__(kFinThreads, 12) finalize_kernel(const Finaliz
         if (i + q < r1) bin1((int)((o4 >> (8 * q)) & 0xFFu), w4[q]);
     }
   };
-  // thread tid takes record groups r0 + 4 (tid + j T): one 32-bit load of four orders and one
-  // vector load of four weights per group, the next group in flight while this one is binned
-  unsigned long long i = r0 + 4ull * tid;
-  uint32_t oa = 0;
-  Acc wa[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-  if (i < r1) {
-    oa = __ldcs(reinterpret_cast<const uint32_t *>(f.rec_o + i));
-    load4(rw + i, wa);
-  }
+  // thread tid takes record groups r0 + 4 (tid + j T), j = 0, 1, ...: one 32-bit load of four orders
+  // and one vector load of four weights per group, G groups loaded before any is binned (enough
+  // loads in flight to cover the memory latency), binned in index order
 #pragma unroll 1
-  while (i < r1) {
-    const unsigned long long in = i + 4ull * T;
-    uint32_t ob = 0;
-    Acc wb[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-    if (in < r1) {
-      ob = __ldcs(reinterpret_cast<const uint32_t *>(f.rec_o + in));
-      load4(rw + in, wb);
-    }
-    bin(oa, wa, i);
-    i = in;
-    oa = ob;
+  for (unsigned long long i0 = r0 + 4ull * tid; i0 < r1; i0 += 4ull * T * G) {
+    uint32_t og[G];
+    Acc wg[G][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) wa[q] = wb[q];
+    for (int g = 0; g < G; ++g) {
+      const unsigned long long i = i0 + 4ull * T * g;
+      og[g] = 0u;
+      wg[g][0] = wg[g][1] = wg[g][2] = wg[g][3] = Acc(0);
+      if (i < r1) {
+        og[g] = __ldcs(reinterpret_cast<const uint32_t *>(f.rec_o + i));
+        load4(rw + i, wg[g]);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const unsigned long long i = i0 + 4ull * T * g;
+      if (i < r1) bin(og[g], wg[g], i);
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -212,37 +216,29 @@ __global__ void __launch_bounds__(kFinThreads, 12) finalize_kernel(const Finaliz
     part[2 * R + K + 1] = 0.0;
     part[3 * R + K + 1] = (double)c;
   }
-  // publish this chunk (its writers fence); the point's last chunk to finish completes the point
-  if (lane == 0) __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const uint32_t nch = f.chunk_prefix[pt + 1] - f.chunk_prefix[pt];
-    s_last = atomicAdd(f.done + pt, 1u) == nch - 1u;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  // this launch has all its chunks of the point; is the point complete?
-  const uint32_t ntot = f.ntotal ? f.ntotal[pt] : f.ntrees[pt];
-  if (cfirst + f.ntrees[pt] != ntot) return;  // more trees in a later launch: partials stay resident
-  __threadfence();
-  const uint32_t nch = ntot == 0u ? 1u : (ntot + kBinChunk - 1) / kBinChunk;
-  const size_t row = f.out_slot ? f.out_slot[pt] : (size_t)pt;
-  const size_t ostride = f.out_stride ? f.out_stride : (size_t)(K + 1);
-  complete_point(f.part + (size_t)slot0 * pstride, pstride, nch, (double)ntot, K, f.L, f.M, f.u + row,
-                 f.coef ? f.coef + row * ostride : nullptr, f.se ? f.se + row * ostride : nullptr,
-                 f.status ? f.status + row : nullptr, 0, tid, T);
 }
 
-// Completion of points whose solve was stopped early (a cancelled server request): one block per
-// point, from the chunk sums of the trees binned so far, N = the trees those chunks hold; the
-// status carries `extra` (SERIES_PARTIAL).
+// Completion of the points of a launch from their chunk sums: one block per point.
 __global__ void __launch_bounds__(kFinThreads) complete_kernel(const CompleteParams c) {
   const int i = blockIdx.x;
-  const size_t row = c.out_slot[i];
-  complete_point(c.part + (size_t)c.part_slot[i] * c.part_stride, c.part_stride, c.nchunks[i], (double)c.ntrees[i],
-                 c.K, c.L, c.M, c.u + row, c.coef ? c.coef + row * c.out_stride : nullptr,
-                 c.se ? c.se + row * c.out_stride : nullptr, c.status ? c.status + row : nullptr, c.extra_status,
-                 threadIdx.x, kFinThreads);
+  const int K = c.K;
+  const uint32_t slot0 = c.part_slot ? c.part_slot[i] : c.chunk_prefix[i];
+  uint32_t nch, N;
+  if (c.nchunks) {  // a stopped solve: the chunks binned so far
+    nch = c.nchunks[i];
+    N = c.ntrees[i];
+  } else {
+    N = c.ntotal ? c.ntotal[i] : c.ntrees[i];
+    const uint32_t first = c.tree_first ? c.tree_first[i] : 0u;
+    if (first + c.ntrees[i] != N) return;  // more trees in a later launch: the sums stay resident
+    nch = N == 0u ? 1u : (N + kBinChunk - 1) / kBinChunk;
+  }
+  const size_t pstride = c.part_stride ? c.part_stride : (size_t)4 * (K + 2);
+  const size_t ostride = c.out_stride ? c.out_stride : (size_t)(K + 1);
+  const size_t row = c.out_slot ? c.out_slot[i] : (size_t)i;
+  complete_point(c.part + (size_t)slot0 * pstride, pstride, nch, (double)N, K, c.L, c.M, c.u + row,
+                 c.coef ? c.coef + row * ostride : nullptr, c.se ? c.se + row * ostride : nullptr,
+                 c.status ? c.status + row : nullptr, c.extra_status, threadIdx.x, kFinThreads);
 }
 
 cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream) {
@@ -251,14 +247,20 @@ cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// One warp per series (pade_value_warp); 4 series per block.
 __global__ void pade_kernel(int n, int K, int L, int M, const double *coef, double *u, int32_t *status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double a[kMaxK + 1];
-  for (int j = 0; j <= L + M; ++j) a[j] = coef[(size_t)i * (K + 1) + j];
+  __shared__ double s_a[4][kMaxK + 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 4 + w;
+  if (i >= n) return;  // whole warps leave together
+  if (lane <= L + M) s_a[w][lane] = coef[(size_t)i * (K + 1) + lane];
+  __syncwarp();
   int st = 0;
-  u[i] = pade_value(a, L, M, &st);
-  if (status) status[i] = st;
+  const double v = pade_value_warp(s_a[w], L, M, &st, lane);
+  if (lane == 0) {
+    u[i] = v;
+    if (status) status[i] = st;
+  }
 }
 
 // First-order statistical error of the Pade value: with the coefficients' standard errors
@@ -343,10 +345,12 @@ cudaError_t launch_pade_error(int n, int K, int L, int M, const double *coef, co
 }
 
 template <typename Acc> static cudaError_t launch_finalize_t(const FinalizeParams &f, cudaStream_t stream) {
-  const size_t smem = (size_t)(f.K + 1) * kFinThreads * sizeof(Acc4<Acc>);
-  cudaError_t e = cudaFuncSetAttribute(finalize_kernel<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int T = kBinThreads, G = kBinGroups;
+  const size_t smem = (size_t)(f.K + 1) * T * sizeof(Acc4<Acc>);
+  auto kern = finalize_kernel<Acc, T, G>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  finalize_kernel<Acc><<<f.total_chunks, kFinThreads, smem, stream>>>(f);
+  kern<<<f.total_chunks, T, smem, stream>>>(f);
   return cudaGetLastError();
 }
 
@@ -358,7 +362,7 @@ cudaError_t launch_finalize(bool fp64, const FinalizeParams &f, cudaStream_t str
 cudaError_t launch_pade(int n, int K, int L, int M, const double *coef, double *u, int32_t *status,
                         cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  pade_kernel<<<(n + 127) / 128, 128, 0, stream>>>(n, K, L, M, coef, u, status);
+  pade_kernel<<<(n + 3) / 4, 128, 0, stream>>>(n, K, L, M, coef, u, status);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ namespace grt {
 
 struct WalkParams;
 
+// The binning kernel: tree records -> per-chunk sums.
 struct FinalizeParams {
   const void *rec_w;         // [total trees] tree weights (float or double)
   const uint8_t *rec_o;      // [total trees] tree orders (K+1 = pruned)
@@ -18,19 +19,12 @@ struct FinalizeParams {
   const uint32_t *chunk_prefix;  // [n+1] first binning chunk of each point in this launch (every point has >= 1)
   uint32_t total_chunks;
   double *part;              // per-chunk sums S1, S2, S|W|, count: [slot][4][K+2], slot stride part_stride
-  uint32_t *done;            // [n] chunks of each point finished (zeroed before the launch)
-  // incremental solves (all null for a one-shot solve):
+  // incremental solves (null / 0 for a one-shot solve):
   const uint32_t *tree_first;  // [n] first tree of this launch's range (a multiple of kBinChunk), null: 0
-  const uint32_t *ntotal;      // [n] the point's whole budget, null: ntrees (the point completes here)
   const uint32_t *part_slot;   // [n] first chunk slot of the point in `part`, null: chunk_prefix[p]
-  const uint32_t *out_slot;    // [n] output row of the point, null: p
   size_t part_stride;          // doubles between chunk slots, 0: 4 (K+2)
-  size_t out_stride;           // doubles between coef / se rows, 0: K+1
-  int n, K, L, M;
-  double *u;                 // [n]
-  double *coef, *se;         // [n][K+1] or null
-  int32_t *status;
-  unsigned long long *stats; // [1] splitting events (sum of record orders), [2] pruned trees: added here           // [n] or null
+  int n, K;
+  unsigned long long *stats; // [1] splitting events (sum of record orders), [2] pruned trees: added here
 };
 
 // Launch shape of the walk kernel (results do not depend on it).
@@ -64,19 +58,24 @@ cudaError_t launch_trees(bool fp64, int dim, int strategy, const WalkParams &p, 
                          uint64_t *hash, cudaStream_t stream);
 cudaError_t launch_finalize(bool fp64, const FinalizeParams &f, cudaStream_t stream);
 
-// Completion of points from the chunk sums binned so far (a stopped solve): one block per point.
+// Completion of points from their chunk sums (after the binning, or for a stopped solve): one block
+// per point adds the point's chunk sums in chunk order and forms a_n, SE_n and the Pade.
 struct CompleteParams {
   int n, K, L, M;
-  const double *part;        // resident chunk sums, slots part_stride doubles apart
+  const double *part;        // chunk sums, slots part_stride doubles apart (0: 4 (K+2))
   size_t part_stride;
-  const uint32_t *part_slot; // [n] first chunk slot of each point
-  const uint32_t *nchunks;   // [n] chunks binned
-  const uint32_t *ntrees;    // [n] trees those chunks hold (N of the estimate)
-  const uint32_t *out_slot;  // [n] output row
-  size_t out_stride;         // doubles between coef / se rows
-  double *u, *coef, *se;
-  int32_t *status;
-  int extra_status;          // bits added to every point's status
+  const uint32_t *part_slot; // [n] first chunk slot of each point, or null: chunk_prefix[i]
+  const uint32_t *chunk_prefix;  // [n+1] (when part_slot is null)
+  const uint32_t *nchunks;   // [n] chunks to add (a stopped solve), or null: those of the whole budget
+  const uint32_t *ntrees;    // [n] with nchunks: the trees those chunks hold; else the trees of the launch
+  const uint32_t *ntotal;    // [n] whole budget, or null: ntrees
+  const uint32_t *tree_first;  // [n] first tree of the launch's range, or null (0); a point whose
+                               // range does not reach its budget is left for a later launch
+  const uint32_t *out_slot;  // [n] output row, or null: i
+  size_t out_stride;         // doubles between coef / se rows (0: K+1)
+  double *u, *coef, *se;     // coef / se may be null
+  int32_t *status;           // may be null
+  int extra_status;          // bits added to every completed point's status
 };
 cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream);
 

@@ -4,6 +4,7 @@
 // one-launch-per-point FP64 path.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -147,6 +148,126 @@ __device__ inline double pade_value(const double *a, int L, int M, int *status) 
     double al = 0.0;
     const int jm = i < Mc ? i : Mc;
     for (int j = 0; j <= jm; ++j) al += beta[j] * c[i - j];
+    P = P * rho + al;
+  }
+  if (fabs(Q) < 1e-8) st |= 2;  // PADE_POLE_NEAR
+  *status = st;
+  return P / Q;
+}
+
+// The same [L/M] Pade, evaluated by all 32 lanes of a warp together (every lane gets the value and
+// the status).  Lane r + 16 h holds row r of the Toeplitz system, columns 9h .. 9h+8 (M <= 16 rows,
+// M + 1 <= 17 columns); an elimination step broadcasts the pivot row and each row's multiplier by
+// shuffles, so its depth is one update instead of M - k of them.  The pivot search, the singularity
+// rule, the back substitution and Horner read the same values in the same order as pade_value (every
+// lane reads them through shuffles from the lanes that hold them), so decisions and values are those
+// of the one-thread evaluation.  `a` [L+M+1] must be readable by every lane (shared memory).
+__device__ inline double pade_value_warp(const double *a, int L, int M, int *status, int lane) {
+  const int n = L + M;
+  const int r = lane & 15, h = lane >> 4;
+  // rescaling: the root test on the binary exponents, as in pade_value
+  const bool nz = lane <= n && pd_abs_bits(a[lane <= n ? lane : 0]) != 0;
+  const unsigned nzm = __ballot_sync(kFull, nz);
+  const int first = nzm ? __ffs((int)nzm) - 1 : n + 1;
+  int q = INT_MIN;
+  if (nz && lane > first) {
+    const int num = pd_ilogb(a[lane]) - pd_ilogb(a[first]), den = lane - first;
+    q = num > 0 ? (num + den - 1) / den : -((-num) / den);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) q = max(q, __shfl_xor_sync(kFull, q, off));
+  const int k = q == INT_MIN ? 0 : q;
+  const double rho = scalbn(1.0, k);
+  const double cl = lane <= n ? pd_scalbn(a[lane], -k * lane) : 0.0;  // c_lane
+  auto c_at = [&](int i) { return __shfl_sync(kFull, cl, i & 31); };  // c_i in every lane (uniform i)
+
+  int st = 0;
+  int Lc = L, Mc = M;
+  double beta[kMaxK + 1];
+  beta[0] = 1.0;
+  while (Mc > 0) {
+    double T[9];  // T[r][9h + e]
+    uint64_t bigk = 0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const int j = 9 * h + e;
+      const int idx = j < Mc ? Lc + r - j : Lc + r + 1;
+      const double v = __shfl_sync(kFull, cl, idx < 0 ? 0 : (idx & 31));
+      double t = 0.0;
+      if (r < Mc && j < Mc) t = idx >= 0 ? v : 0.0;
+      if (r < Mc && j == Mc) t = -v;
+      T[e] = t;
+      if (r < Mc && j < Mc) bigk = max(bigk, pd_key(t));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bigk = max(bigk, (uint64_t)__shfl_xor_sync(kFull, (unsigned long long)bigk, off));
+    bool ok = bigk > 0;
+    const uint64_t tiny = pd_key(1e-14 * __longlong_as_double((long long)bigk));
+    auto elem = [&](int col) {  // this lane's T[r][col] (col in its half)
+      double v = T[0];
+#pragma unroll
+      for (int e = 1; e < 9; ++e)
+        if (e == col % 9) v = T[e];
+      return v;
+    };
+    for (int kk = 0; kk < Mc && ok; ++kk) {
+      const int hk = kk / 9;
+      const double colk = elem(kk);
+      // pivot search on column kk, rows kk .. Mc-1, in row order (every lane scans the same values)
+      int pr = kk;
+      const uint64_t b0 = pd_abs_bits(__shfl_sync(kFull, colk, kk + 16 * hk));
+      if (b0 <= 0x7FF0000000000000ull) {  // a NaN pivot candidate keeps its row
+        uint64_t pvk = b0;
+        for (int rr = kk + 1; rr < Mc; ++rr) {
+          const uint64_t vk = pd_key(__shfl_sync(kFull, colk, rr + 16 * hk));
+          if (vk > pvk) {
+            pvk = vk;
+            pr = rr;
+          }
+        }
+        if (pvk <= tiny) {
+          ok = false;
+          break;
+        }
+      }
+      if (pr != kk) {  // swap rows kk and pr (whole rows: the entries left of kk are not read again)
+        const int src = (r == kk ? pr : (r == pr ? kk : r)) + 16 * h;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) T[e] = __shfl_sync(kFull, T[e], src);
+      }
+      const double inv = 1.0 / __shfl_sync(kFull, elem(kk), kk + 16 * hk);
+      const double mine = elem(kk) * inv;             // the multiplier of this lane's row, in half hk
+      const double m = __shfl_sync(kFull, mine, r + 16 * hk);
+      double tk[9];                                   // the pivot row's entries of this half
+#pragma unroll
+      for (int e = 0; e < 9; ++e) tk[e] = __shfl_sync(kFull, T[e], kk + 16 * h);
+      if (r > kk && r < Mc && pd_abs_bits(m) != 0) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          const int j = 9 * h + e;
+          if (j >= kk && j <= Mc) T[e] -= m * tk[e];
+        }
+      }
+    }
+    if (ok) {
+      for (int rr = Mc - 1; rr >= 0; --rr) {
+        double sv = __shfl_sync(kFull, elem(Mc), rr + 16 * (Mc / 9));
+        for (int j = rr + 1; j < Mc; ++j) sv -= __shfl_sync(kFull, elem(j), rr + 16 * (j / 9)) * beta[j + 1];
+        beta[rr + 1] = sv / __shfl_sync(kFull, elem(rr), rr + 16 * (rr / 9));
+      }
+      break;
+    }
+    st |= 1;  // PADE_SINGULAR
+    --Mc;
+    if (Lc > 0) --Lc;
+  }
+  double Q = 0.0;
+  for (int j = Mc; j >= 0; --j) Q = Q * rho + beta[j];
+  double P = 0.0;
+  for (int i = Lc; i >= 0; --i) {
+    double al = 0.0;
+    const int jm = i < Mc ? i : Mc;
+    for (int j = 0; j <= jm; ++j) al += beta[j] * c_at(i - j);
     P = P * rho + al;
   }
   if (fabs(Q) < 1e-8) st |= 2;  // PADE_POLE_NEAR

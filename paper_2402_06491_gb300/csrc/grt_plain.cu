@@ -157,12 +157,14 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(const WalkParams p
     if (q.se) q.se[n] = var > 0.0 ? sqrt(var) : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // the first warp evaluates the Pade together
     int st = 0;
-    const double u = pade_value(s_a, q.L, q.M, &st);
-    if (N > 0.0 && s_tot[0][K + 1] > 0.01 * N) st |= 8;  // HIGH_PRUNE
-    *q.u = u;
-    if (q.status) *q.status = st;
+    const double u = pade_value_warp(s_a, q.L, q.M, &st, threadIdx.x);
+    if (threadIdx.x == 0) {
+      if (N > 0.0 && s_tot[0][K + 1] > 0.01 * N) st |= 8;  // HIGH_PRUNE
+      *q.u = u;
+      if (q.status) *q.status = st;
+    }
   }
 }
 

@@ -324,23 +324,33 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     f.chunk_prefix = d_cpre;
     f.total_chunks = (uint32_t)chunks;
     f.part = part_pool.as<double>();
-    f.done = reinterpret_cast<uint32_t *>(d_work + 64);
     f.tree_first = d_first;
-    f.ntotal = d_ntot;
     f.part_slot = d_pslot;
-    f.out_slot = d_oslot;
     f.part_stride = kPartStride;
-    f.out_stride = kOutStride;
     f.n = (int)n;
     f.K = K;
-    f.L = r0->L;
-    f.M = r0->M;
-    f.u = out_u.as<double>();
-    f.coef = out_coef.as<double>();
-    f.se = out_se.as<double>();
-    f.status = out_status.as<int32_t>();
     f.stats = w.stats;
     if (e == cudaSuccess) e = grt::launch_finalize(fp64, f, st);
+    ++launches;
+    // points whose last range was in this group: chunk sums -> a_n, SE_n, Pade
+    grt::CompleteParams cpl{};
+    cpl.n = (int)n;
+    cpl.K = K;
+    cpl.L = r0->L;
+    cpl.M = r0->M;
+    cpl.part = part_pool.as<double>();
+    cpl.part_stride = kPartStride;
+    cpl.part_slot = d_pslot;
+    cpl.ntrees = d_ntrees;
+    cpl.ntotal = d_ntot;
+    cpl.tree_first = d_first;
+    cpl.out_slot = d_oslot;
+    cpl.out_stride = kOutStride;
+    cpl.u = out_u.as<double>();
+    cpl.coef = out_coef.as<double>();
+    cpl.se = out_se.as<double>();
+    cpl.status = out_status.as<int32_t>();
+    if (e == cudaSuccess) e = grt::launch_complete(cpl, st);
     ++launches;
     if (e != cudaSuccess) {
       why = std::string("step launch: ") + cudaGetErrorString(e);

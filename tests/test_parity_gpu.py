@@ -331,7 +331,7 @@ def test_device_resident_plan_matches_host_solve(grt):
     assert pruned == int(o["cnt"][:, K + 1].sum())
     cnt = o["cnt"].astype(np.int64)
     assert splits == int((cnt[:, : K + 2] * np.arange(K + 2)).sum())
-    assert grt.grt_plan_launches(plan) == 2
+    assert grt.grt_plan_launches(plan) == 3  # the walk, the binning and the completion
     plan.close()
     ctx.close()
 
