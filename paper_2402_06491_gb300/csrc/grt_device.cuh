@@ -483,20 +483,21 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
                                           NodeOut<Real, DIM> &o) {
   using M = Math<Real>;
   const uint4 w = philox4x32_10(make_uint4(id_lo, id_hi, tree, point), p.rk0, p.rk1);
-  // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2)
+  // Box-Muller on (w2, w3): n0 = r cos(2 pi U3), n1 = r sin(2 pi U3), r = sqrt(-2 ln U2); the
+  // segment below scales them by sqrt(2 D s), taken together with r as one square root
   using F = Node<Real>;
-  Real n[DIM];
+  Real lg[DIM > 2 ? 2 : 1], cs[DIM];  // -2 ln U of each Box-Muller pair; cos / sin of its angle
   {
-    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w.z)));
+    lg[0] = F::neg2ln(uniform01<Real>(w.z));
     Real s, c;
     F::sincos2pi_w(w.w, &s, &c);
-    n[0] = r * c;
-    if (DIM > 1) n[DIM > 1 ? 1 : 0] = r * s;
+    cs[0] = c;
+    if (DIM > 1) cs[DIM > 1 ? 1 : 0] = s;
   }
   if (DIM == 3) {
     const uint4 w2 = philox4x32_10(make_uint4(id_lo, id_hi, tree | 0x80000000u, point), p.rk0, p.rk1);
-    const Real r = F::sqrt_pos(F::neg2ln(uniform01<Real>(w2.x)));
-    n[DIM - 1] = r * F::cos2pi_w(w2.y);
+    lg[DIM > 2 ? 1 : 0] = F::neg2ln(uniform01<Real>(w2.x));
+    cs[DIM - 1] = F::cos2pi_w(w2.y);
   }
 
   bool leaf;
@@ -522,9 +523,12 @@ __device__ __forceinline__ void node_step(const WalkParams &p, const Real *__res
     for (int i = 0; i < DIM; ++i) o.y[i] = x[i];
     euler_segment<Real, DIM>(p, xp, seg, id_lo, id_hi, tree, point, o.y);
   } else {
-    const Real sc = F::sqrt_pos(Scalars<Real>::two_D(p) * seg);
+    // y = x + sqrt(2 D s) r (cos, sin): the two square roots as one
+    const Real tds = Scalars<Real>::two_D(p) * seg;
+    const Real R0 = F::sqrt_pos(tds * lg[0]);
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) o.y[i] = x[i] + sc * n[i];
+    for (int i = 0; i < (DIM < 2 ? DIM : 2); ++i) o.y[i] = x[i] + R0 * cs[i];
+    if constexpr (DIM == 3) o.y[2] = x[2] + F::sqrt_pos(tds * lg[1]) * cs[2];
   }
 
   // every lane evaluates g (a leaf uses it) and reads its term factor (a split uses it):
