@@ -160,8 +160,8 @@ __device__ inline double pade_value(const double *a, int L, int M, int *status) 
 // M + 1 <= 17 columns); an elimination step broadcasts the pivot row and each row's multiplier by
 // shuffles, so its depth is one update instead of M - k of them.  The pivot search, the singularity
 // rule, the back substitution and Horner read the same values in the same order as pade_value (every
-// lane reads them through shuffles from the lanes that hold them), so decisions and values are those
-// of the one-thread evaluation.  `a` [L+M+1] must be readable by every lane (shared memory).
+// lane reads them through shuffles from the lanes that hold them) and apply the same operations.
+// `a` [L+M+1] must be readable by every lane (shared memory).
 __device__ inline double pade_value_warp(const double *a, int L, int M, int *status, int lane) {
   const int n = L + M;
   const int r = lane & 15, h = lane >> 4;
