@@ -243,61 +243,63 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
       ++depth;
     }
     const bool up = !down && !pruned && depth > 0;
-    if (down) {  // first child: label 16 id + 1
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) x[i] = o.y[i];
-      tau = o.tau_c;
-      id_hi = __funnelshift_l(id_lo, id_hi, 4);
-      id_lo = (id_lo << 4) | 1u;
-      ++tdep;
-    }
-    if (up) {  // the next child of the frame on top; a frame whose last child this is is popped
-      // (its digit is still advanced: the slot is free, and a push overwrites all of it)
-      const int lvl = depth - 1;
+    if (down || up) {
+      // the next node: the first child (down) or the next child of the frame on top (up); a frame
+      // whose last child this is is popped (its digit is still advanced: the slot is free, and a
+      // push overwrites all of it).  nk = (tree depth F of the parent << 16) | (k << 8) | digit:
+      // a first child has parent depth tdep and digit 1
       uint32_t nk;
-      if (SLEV == 0 || lvl < lv) {
-        const int at = lvl * 32 + lane;
-        if constexpr (kVec) {
-          const float4 a = fr_a[at];
-          if constexpr (DIM <= 2) {
-            x[0] = (Real)a.x;
-            if (DIM > 1) x[DIM - 1] = (Real)a.y;
-            tau = (Real)a.z;
-            nk = __float_as_uint(a.w);
-            reinterpret_cast<uint32_t *>(fr_a)[4 * at + 3] = nk + 1u;
+      if (up) {
+        const int lvl = depth - 1;
+        if (SLEV == 0 || lvl < lv) {
+          const int at = lvl * 32 + lane;
+          if constexpr (kVec) {
+            const float4 a = fr_a[at];
+            if constexpr (DIM <= 2) {
+              x[0] = (Real)a.x;
+              if (DIM > 1) x[DIM - 1] = (Real)a.y;
+              tau = (Real)a.z;
+              nk = __float_as_uint(a.w);
+              reinterpret_cast<uint32_t *>(fr_a)[4 * at + 3] = nk + 1u;
+            } else {
+              x[0] = (Real)a.x;
+              x[1] = (Real)a.y;
+              x[DIM - 1] = (Real)a.z;
+              tau = (Real)a.w;
+              nk = fr_m[at];
+              fr_m[at] = nk + 1u;
+            }
           } else {
-            x[0] = (Real)a.x;
-            x[1] = (Real)a.y;
-            x[DIM - 1] = (Real)a.z;
-            tau = (Real)a.w;
-            nk = fr_m[at];
-            fr_m[at] = nk + 1u;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
+            tau = stk_tau[at];
+            nk = stk_nk[at];
+            stk_nk[at] = nk + 1u;
           }
         } else {
+          const int at = lvl - lv;
 #pragma unroll
-          for (int i = 0; i < DIM; ++i) x[i] = stk_y[(size_t)i * lv * 32 + at];
-          tau = stk_tau[at];
-          nk = stk_nk[at];
-          stk_nk[at] = nk + 1u;
+          for (int i = 0; i < DIM; ++i) x[i] = ly[at][i];
+          tau = ltau[at];
+          nk = lnk[at];
+          lnk[at] = nk + 1u;
         }
+        if ((nk & 0xFFu) == ((nk >> 8) & 0xFFu)) --depth;
       } else {
-        const int at = lvl - lv;
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) x[i] = ly[at][i];
-        tau = ltau[at];
-        nk = lnk[at];
-        lnk[at] = nk + 1u;
+        for (int i = 0; i < DIM; ++i) x[i] = o.y[i];
+        tau = o.tau_c;
+        nk = (tdep << 16) | 1u;
       }
-      // the child's label: the split node's label (the current label without its last
-      // tdep - F digits) followed by the child's digit
-      const uint32_t nd = nk & 0xFFu, F = nk >> 16;
-      const uint32_t sh = 4u * (tdep - F);  // 4 .. 64
-      const uint64_t id = ((uint64_t)id_hi << 32) | id_lo;
-      const uint64_t idF = sh >= 64u ? 0ull : (id >> sh);
-      id_lo = ((uint32_t)idF << 4) | nd;
+      // the child's label: the parent's label (the current label without its last tdep - F
+      // digits; for a first child the current label itself) followed by the child's digit
+      const uint32_t F = nk >> 16;
+      const uint32_t sh = 4u * (tdep - F);  // 0 .. 64; shr.b64 clamps 64 to an all-zero result
+      uint64_t idF;
+      asm("shr.b64 %0, %1, %2;" : "=l"(idF) : "l"(((uint64_t)id_hi << 32) | id_lo), "r"(sh));
+      id_lo = ((uint32_t)idF << 4) | (nk & 0xFFu);
       id_hi = (uint32_t)(idF >> 28);
       tdep = F + 1u;
-      if (nd == ((nk >> 8) & 0xFFu)) --depth;
     }
     if (!down && !up) {  // leaf with nothing pending, or pruned
       reinterpret_cast<Real *>(p.rec_w)[rec] = pruned ? Real(0) : W;
