@@ -498,7 +498,7 @@ def _serve_trace(grt, dev: int, probs: dict, ctxs: dict, trace: list) -> dict:
 
 
 def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, plain_requests: int,
-                  plain_cap_s: float, overload_requests: int = 100) -> dict:
+                  plain_cap_s: float, overload_requests: int = 2000) -> dict:
     probs = workloads.serving_problems("fp32")
     ctxs = {k: grt.grt_create(v["problem"], dev) for k, v in probs.items()}
     mean_trees = workloads.serving_mean_trees()
@@ -508,14 +508,15 @@ def serving_bench(grt, dev: int, capacity_trees_per_s: float, n_requests: int, p
     lat = run.pop("lat")
     out = dict(trace=(f"{len(trace)} Poisson requests at {rate:.1f} req/s (0.7 x the measured sin_2d capacity / mean "
                       f"request of {mean_trees:.3g} trees); 1-4096 points log-uniform, 1e3-1e7 trees per point "
-                      f"log-uniform; f in (u^2-u, sin u, u-u^3) x d in (1, 2, 3); 16 GB admission budget; "
-                      f"2^26-tree steps"), **run)
+                      f"log-uniform; f in (u^2-u, sin u, u-u^3) x d in (1, 2, 3); one service-wide seed, "
+                      f"disjoint point streams per request; 16 GB admission budget; 2^26-tree steps"), **run)
     if overload_requests > 0:
         # the configured arrival rate, 2000 req/s: ~20x what one GPU serves at these budgets, so the
         # requests queue (admission by memory, smallest remaining work first)
-        over = _serve_trace(grt, dev, probs, ctxs, workloads.serving_trace(overload_requests, 2000.0, seed=1))
+        over = _serve_trace(grt, dev, probs, ctxs, workloads.serving_trace(overload_requests, 2000.0, seed=0))
         over.pop("lat")
-        out["at_configured_rate"] = dict(trace=f"{overload_requests} Poisson requests at 2000 req/s, same mix", **over)
+        out["at_configured_rate"] = dict(trace=f"the first {overload_requests} Poisson arrivals at 2000 req/s "
+                                               f"(seed 0), same mix", **over)
     # plain path: one FP64 launch per point (grt_solve_plain), requests first come first served, same arrivals
     ctx64 = {k: grt.grt_create(dict(v["problem"], precision="fp64"), dev) for k, v in probs.items()}
     for k, v in probs.items():  # warm-up
@@ -841,7 +842,7 @@ def gpu_arm(args) -> int:
                                      "err_over_1e-2": h["err_over_1e-2"]}
     if not args.no_serving and world == 1:
         srv = serving_bench(grt, gpu, value / world, args.serving_requests, args.plain_requests,
-                            float(os.environ.get("GRT_PLAIN_CAP_S", "30")))
+                            float(os.environ.get("GRT_PLAIN_CAP_S", "30")), args.overload_requests)
         details["serving"] = srv
         line["serving"] = serving_summary(srv)
     if world == 1 and not args.no_cpu_baseline:
@@ -877,7 +878,8 @@ def serving_summary(srv: dict) -> dict:
     for key in ("shared_launch_steps", "at_configured_rate"):
         if key in srv:
             v = srv[key]
-            out[key] = {k: v.get(k) for k in ("p50_ms", "p99_ms", "points_per_s")} if isinstance(v, dict) else v
+            out[key] = ({k: v.get(k) for k in ("p50_ms", "p99_ms", "points_per_s", "shared_launches")}
+                        if isinstance(v, dict) else v)
     return out
 
 
@@ -932,6 +934,8 @@ def main() -> int:
                     help="fixed walk launch shape 'warps,smem_levels,blocks_per_sm,tile' instead of the autotuner")
     ap.add_argument("--serving-requests", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=20)
+    ap.add_argument("--overload-requests", type=int, default=2000,
+                    help="requests of the trace replayed at the configured 2000 req/s (0: skip it)")
     ap.add_argument("--details", default="bench_details.json",
                     help="side JSON file for the per-result and per-workload figures ('' = none)")
     args = ap.parse_args()

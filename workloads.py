@@ -244,11 +244,15 @@ def serving_problems(precision: str = "fp32") -> dict:
 def serving_trace(n_requests: int, rate_per_s: float, seed: int = 0, max_points: int = 4096,
                   trees_lo: float = 1e3, trees_hi: float = 1e7) -> list:
     """Seeded Poisson arrivals; points per request log-uniform in [1, max_points], tree budgets
-    per point log-uniform in [trees_lo, trees_hi], problem uniform over serving_problems()."""
+    per point log-uniform in [trees_lo, trees_hi], problem uniform over serving_problems().
+    The requests draw from one service-wide stream key (Philox key = the trace's seed) and get
+    disjoint point streams (point_base = the points of the requests before them), so requests
+    of the same problem and orders may share a walk launch."""
     rng = np.random.default_rng(seed)
     keys = sorted(serving_problems().keys())
     t_arr = 0.0
     out = []
+    base = 0
     for k in range(n_requests):
         t_arr += rng.exponential(1.0 / rate_per_s)
         key = keys[int(rng.integers(0, len(keys)))]
@@ -257,7 +261,8 @@ def serving_trace(n_requests: int, rate_per_s: float, seed: int = 0, max_points:
         x = rng.uniform(-3.0, 3.0, size=(n, d))
         t = rng.uniform(0.1, 1.0, size=n)
         nt = np.exp(rng.uniform(math.log(trees_lo), math.log(trees_hi), size=n)).astype(np.uint64)
-        out.append(dict(arrival=t_arr, key=key, x=x, t=t, ntrees=nt, seed=k, point_base=0))
+        out.append(dict(arrival=t_arr, key=key, x=x, t=t, ntrees=nt, seed=seed, point_base=base))
+        base += n
     return out
 
 
