@@ -292,23 +292,31 @@ int grt_trees(grt_ctx *ctx, const double *x, double t, uint64_t point_index, uin
  * A server owns a scheduler thread and a device-memory budget on one device.
  * Requests (a problem context, points, per-point tree budgets, K, L, M, seed)
  * may be submitted at any time from any thread; each is admitted when its
- * resident state (per-point chunk sums of 8192 trees, result rows) fits the
- * budget, first come first admitted.  The scheduler runs the GPU in steps of at
- * most `step_trees` trees taken from all admitted requests, smallest remaining
- * work first, in ranges that start on a point's 8192-tree boundaries; requests
- * of one problem, K, L, M and seed share one walk and one binning launch per
- * step; the groups of one step run concurrently on several streams.  A point's
- * result is identical, bit for bit, to grt_solve of the same point (same
- * point_base + index and seed), alone or in any mix.  Batching happens at step
- * boundaries: a request that arrives while others run joins the next step
- * (steps of at most step_trees trees, a few milliseconds at full load).
- * Contexts passed to grt_submit must outlive their requests. */
+ * resident state fits the budget, first come first admitted: per point one
+ * accumulator (for every order and statistic, the compensated sum of the
+ * point's per-8192-tree chunk sums so far) and its result row.  The scheduler
+ * runs the GPU in steps of at most `step_trees` trees taken from all admitted
+ * requests, smallest remaining work first, in ranges that start on a point's
+ * 8192-tree boundaries; requests of one problem, K, L, M and seed share one
+ * walk and one binning launch per step; the groups of one step run
+ * concurrently on several streams.  A point's result is identical, bit for
+ * bit, to grt_solve of the same point (same point_base + index and seed),
+ * alone or in any mix.  Batching happens at step boundaries: a request that
+ * arrives while others run joins the next step (steps of at most step_trees
+ * trees, a few milliseconds at full load).  Contexts passed to grt_submit must
+ * outlive their requests. */
 typedef struct grt_server grt_server;
 
-/* mem_budget_bytes: device memory for step buffers and resident state (at least
- * 9 (step_trees + 4 P + 64) + 312 P + 65 KB + 1 MB bytes, P = step points =
- * clamp(step_trees / 256, 4096, 2^20)); step_trees: trees per step (0: 2^27).
- * GRT_EINVAL if the budget is too small, GRT_ENOMEM / GRT_EDEVICE on failure. */
+/* Memory of a server with steps of step_trees trees (0: 2^27): *step_bytes for
+ * its step buffers, *point_bytes per admitted point (either may be NULL).  A
+ * server with budget B admits floor((B - step_bytes) / point_bytes) points at a
+ * time.  GRT_EINVAL for step_trees outside [8192, 2^31]. */
+int grt_server_sizes(uint64_t step_trees, uint64_t *step_bytes, uint64_t *point_bytes);
+
+/* mem_budget_bytes: device memory for step buffers and resident state, at
+ * least step_bytes (grt_server_sizes) + 1 MiB; step_trees: trees per step
+ * (0: 2^27).  GRT_EINVAL if the budget is too small, GRT_ENOMEM / GRT_EDEVICE
+ * on failure. */
 int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees, grt_server **out);
 
 /* Stop the scheduler (after its current step) and free the server and any

@@ -118,6 +118,7 @@ def _load():
         "grt_plan_kappa": ([_vp, _vp, _vp], i32),
         "grt_trees": ([_vp, f64p, ctypes.c_double, u64, u64, u64, i32, u64, i32p, f64p, u32p, u64p], i32),
         "grt_solve_noalloc": ([_vp, i64, _vp, _vp, u64p, i32, i32, i32, u64, u64, _vp, _vp, _vp, _vp, _vp], i32),
+        "grt_server_sizes": ([u64, u64p, u64p], i32),
         "grt_server_create": ([i32, u64, u64, _P(_vp)], i32),
         "grt_server_destroy": ([_vp], None),
         "grt_server_last_error": ([_vp], ctypes.c_char_p),
@@ -528,6 +529,15 @@ def _check_server(rc: int, server: "Server"):
         raise GrtError(rc, msg.decode() if msg else "")
 
 
+def grt_server_sizes(step_trees: int = 0) -> dict:
+    """Step-buffer bytes of a server with steps of step_trees trees and resident bytes per admitted point."""
+    sb, pb = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = _load().grt_server_sizes(int(step_trees), ctypes.byref(sb), ctypes.byref(pb))
+    if rc != OK:
+        raise GrtError(rc, "grt_server_sizes: step_trees must be in [8192, 2^31]")
+    return {"step_bytes": int(sb.value), "point_bytes": int(pb.value)}
+
+
 def grt_server_create(device: int = 0, mem_budget_bytes: int = 2 << 30, step_trees: int = 0) -> Server:
     h = _vp()
     rc = _load().grt_server_create(int(device), int(mem_budget_bytes), int(step_trees), ctypes.byref(h))
@@ -690,7 +700,8 @@ EXPORTED = ["grt_create", "grt_destroy", "grt_last_error", "grt_solve", "grt_sol
             "grt_plan_counters", "grt_plan_set_timing", "grt_plan_timing", "grt_plan_launches", "grt_plan_destroy",
             "grt_plan_set_config", "grt_plan_get_config", "grt_set_solve_config", "grt_plan_autotune", "grt_plan_graph_capture",
             "grt_plan_graph_launch",
-            "grt_pade", "grt_pade_error", "grt_plan_kappa", "grt_trees", "grt_solve_noalloc", "grt_server_create", "grt_server_destroy",
+            "grt_pade", "grt_pade_error", "grt_plan_kappa", "grt_trees", "grt_solve_noalloc", "grt_server_sizes", "grt_server_create",
+            "grt_server_destroy",
             "grt_server_last_error", "grt_submit", "grt_poll", "grt_poll_ex", "grt_cancel", "grt_server_stats",
             "grt_spline_grid",
             "grt_pdd_points", "grt_pdd_solve", "grt_pdd_solve_range"]

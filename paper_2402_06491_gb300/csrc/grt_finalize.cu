@@ -31,24 +31,13 @@ __device__ __forceinline__ void load4(const double *p, double (&w)[4]) {
   w[3] = b.y;
 }
 
-// Completion of one point from its resident per-chunk sums (rows S1, S2, S|W|, count of K+2
-// entries each; chunk slots pstride doubles apart): the first nch chunk sums added in chunk order
-// with compensation, a_n = S1_n / N and SE_n = sqrt((S2_n / N - a_n^2) / (N - 1)) (Sec. 2.4, Eq.
-// simplecase_discrete), the FP64 [L/M] Pade at eps = 1, HIGH_PRUNE when more than 1 % of the N
-// trees were pruned, and the bits `extra`.  All T threads of the block call it (it synchronises).
-__device__ __forceinline__ void complete_point(const double *part0, size_t pstride, uint32_t nch, double N, int K,
-                                               int L, int M, double *u, double *coef, double *se, int32_t *status,
-                                               int extra, int tid, int T) {
-  const int R = K + 2;
-  __shared__ double tot[4][kMaxK + 2];
+// a_n = S1_n / N and SE_n = sqrt((S2_n / N - a_n^2) / (N - 1)) (Sec. 2.4, Eq. simplecase_discrete)
+// from one point's summed rows tot[stat][row] (S1, S2, S|W|, count; block-shared, complete), the
+// FP64 [L/M] Pade at eps = 1, HIGH_PRUNE when more than 1 % of the N trees were pruned, and the
+// bits `extra`.  All threads of the block call it (it synchronises).
+__device__ __forceinline__ void finish_point(const double (*tot)[kMaxK + 2], double N, int K, int L, int M, double *u,
+                                             double *coef, double *se, int32_t *status, int extra, int tid) {
   __shared__ double a[kMaxK + 1];
-  for (int e = tid; e < 4 * R; e += T) {  // entry (stat, row) adds the point's chunk sums in chunk order
-    const double *pp = part0 + e;
-    double s = 0.0, c = 0.0;
-    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
-    tot[e / R][e % R] = s - c;
-  }
-  __syncthreads();
   if (tid <= K) {
     const double an = N > 0.0 ? tot[0][tid] / N : 0.0;
     const double var = N > 1.0 ? (tot[1][tid] / N - an * an) / (N - 1.0) : 0.0;
@@ -68,6 +57,24 @@ __device__ __forceinline__ void complete_point(const double *part0, size_t pstri
       if (status) *status = st;
     }
   }
+}
+
+// Completion of one point from its per-chunk sums (rows S1, S2, S|W|, count of K+2 entries each;
+// chunk slots pstride doubles apart): the first nch chunk sums added in chunk order with
+// compensation, then finish_point.  All T threads of the block call it (it synchronises).
+__device__ __forceinline__ void complete_point(const double *part0, size_t pstride, uint32_t nch, double N, int K,
+                                               int L, int M, double *u, double *coef, double *se, int32_t *status,
+                                               int extra, int tid, int T) {
+  const int R = K + 2;
+  __shared__ double tot[4][kMaxK + 2];
+  for (int e = tid; e < 4 * R; e += T) {  // entry (stat, row) adds the point's chunk sums in chunk order
+    const double *pp = part0 + e;
+    double s = 0.0, c = 0.0;
+    for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * pstride));
+    tot[e / R][e % R] = s - c;
+  }
+  __syncthreads();
+  finish_point(tot, N, K, L, M, u, coef, se, status, extra, tid);
 }
 
 // Shape of the binning kernel: threads per block (one block per 8192-record chunk), record groups
@@ -244,6 +251,53 @@ __global__ void __launch_bounds__(kFinThreads) complete_kernel(const CompletePar
 cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream) {
   if (c.n <= 0) return cudaSuccess;
   complete_kernel<<<(unsigned)c.n, kFinThreads, 0, stream>>>(c);
+  return cudaGetLastError();
+}
+
+// Serving, one block per (point, tree range) unit of a step.  A point's resident accumulator holds,
+// for every entry (stat, row), the compensated sum (s, c) of the chunk sums added so far; the
+// unit's chunk sums are added to it in chunk order.  A point's ranges start on its 8192-tree chunk
+// boundaries and are walked in tree order, so its chunk sums meet the accumulator in chunk order:
+// the same compensated additions, in the same order, as complete_point's loop over all of them, and
+// the point's result is the same bits however its trees were split over steps.  A unit whose range
+// ends the point's budget completes the point (finish_point) into output row `slot`; otherwise the
+// accumulator is written back.
+__global__ void __launch_bounds__(kFinThreads) fold_kernel(const FoldParams f) {
+  __shared__ double tot[4][kMaxK + 2];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const int K = f.K, R = K + 2;
+  const uint32_t slot = f.slot[i], first = f.tree_first[i], N = f.ntotal[i];
+  const bool last = first + f.ntrees[i] == N;  // block-uniform
+  double *as = f.acc + (size_t)slot * f.acc_stride, *ac = as + f.acc_stride / 2;
+  const uint32_t c0 = f.part ? f.chunk_prefix[i] : 0u;
+  const uint32_t nch = f.part ? f.chunk_prefix[i + 1] - c0 : 0u;
+  for (int e = tid; e < 4 * R; e += kFinThreads) {
+    double s = 0.0, c = 0.0;
+    if (first != 0u) {  // the point's earlier ranges
+      s = as[e];
+      c = ac[e];
+    }
+    if (nch > 0u) {
+      const double *pp = f.part + (size_t)c0 * f.part_stride + e;
+      for (uint32_t k = 0; k < nch; ++k) kahan_add(s, c, __ldcg(pp + (size_t)k * f.part_stride));
+    }
+    if (last) {
+      tot[e / R][e % R] = s - c;
+    } else {
+      as[e] = s;
+      ac[e] = c;
+    }
+  }
+  if (!last) return;
+  __syncthreads();
+  const size_t os = f.out_stride;
+  finish_point(tot, (double)N, K, f.L, f.M, f.u + slot, f.coef ? f.coef + (size_t)slot * os : nullptr,
+               f.se ? f.se + (size_t)slot * os : nullptr, f.status ? f.status + slot : nullptr, f.extra_status, tid);
+}
+
+cudaError_t launch_fold(const FoldParams &f, cudaStream_t stream) {
+  if (f.n <= 0) return cudaSuccess;
+  fold_kernel<<<(unsigned)f.n, kFinThreads, 0, stream>>>(f);
   return cudaGetLastError();
 }
 

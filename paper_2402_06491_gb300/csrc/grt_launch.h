@@ -79,6 +79,26 @@ struct CompleteParams {
 };
 cudaError_t launch_complete(const CompleteParams &c, cudaStream_t stream);
 
+// Serving: the chunk sums of one step's (point, tree range) units added to the points' resident
+// accumulators, and the points whose budget the range ends completed (one block per unit).
+struct FoldParams {
+  int n, K, L, M;
+  const double *part;            // the step's chunk sums (slots part_stride doubles apart), or null: none
+  size_t part_stride;
+  const uint32_t *chunk_prefix;  // [n+1] first chunk slot of each unit in part (read only with part)
+  double *acc;                   // accumulators: slot k at acc + k acc_stride, compensated sums s [4 (K+2)]
+  size_t acc_stride;             // then their compensations c at acc_stride / 2
+  const uint32_t *slot;          // [n] accumulator slot = output row of each unit's point
+  const uint32_t *tree_first;    // [n] trees already in the accumulator (0: start from zero sums)
+  const uint32_t *ntrees;        // [n] trees of the unit's range
+  const uint32_t *ntotal;        // [n] the point's N: it completes when tree_first + ntrees == ntotal
+  size_t out_stride;             // doubles between coef / se rows
+  double *u, *coef, *se;
+  int32_t *status;
+  int extra_status;              // bits added to every completed point's status
+};
+cudaError_t launch_fold(const FoldParams &f, cudaStream_t stream);
+
 // The plain FP64 path (grt_plain.cu): one launch per point.
 constexpr int kPlainThreads = 128;
 struct PlainPoint {

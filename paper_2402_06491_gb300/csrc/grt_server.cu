@@ -6,13 +6,15 @@
 // -- smallest remaining work first, up to a step budget -- groups them by
 // problem and series shape, and runs the walk and binning kernels over the
 // group in one launch each, so requests that arrive while others run join the
-// next step and share its launches.  Per-point chunk sums stay resident in
-// device memory between steps; since every range a step takes starts on a
-// binning-chunk boundary of the point's own tree numbering and the chunk sums
-// are added in chunk order when the point completes, a point's result is the
-// same bits whether it was solved alone, in one launch, or over many steps.
-// Admission is by device memory: a request waits until its resident chunk
-// sums and result rows fit the budget.  The groups of one step run on several
+// next step and share its launches.  Each point keeps one resident accumulator
+// in device memory between steps -- per order and statistic, the compensated
+// sum of its chunk sums so far; since every range a step takes starts on a
+// binning-chunk boundary of the point's own tree numbering and a point's
+// ranges are walked in tree order, its chunk sums are added in chunk order, as
+// in a one-shot solve, and a point's result is the same bits whether it was
+// solved alone, in one launch, or over many steps.  Admission is by device
+// memory: a request waits until its points' accumulators and result rows fit
+// the budget (1436 bytes per point).  The groups of one step run on several
 // streams at once (disjoint regions of the step buffers), so the launches of
 // different requests overlap on the device.  A cancelled request stops taking
 // trees after the current step; each of its unfinished points is completed
@@ -40,8 +42,11 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr size_t kPartStride = 4 * (GRT_MAX_K + 2);  // doubles per resident chunk slot
+constexpr size_t kPartStride = 4 * (GRT_MAX_K + 2);  // doubles per chunk-sum slot of a step
+constexpr size_t kAccStride = 2 * kPartStride;       // doubles per resident point accumulator (s, c)
 constexpr size_t kOutStride = GRT_MAX_K + 1;         // doubles per coef / se row
+// resident bytes per admitted point: its accumulator and its result row (u, status, coef, se)
+constexpr size_t kPointBytes = kAccStride * 8 + 8 + 4 + 2 * kOutStride * 8;
 constexpr int kStreams = 4;                          // streams the groups of a step run on
 
 // First-fit allocator of row ranges in [0, capacity).
@@ -105,8 +110,7 @@ struct Request {
   std::vector<uint32_t> N;         // trees per point
   std::vector<uint32_t> done;      // trees walked per point (chunk-aligned until the last range)
   std::vector<uint8_t> complete;   // point finished
-  std::vector<uint32_t> part_slot; // first resident chunk slot per point
-  uint64_t part_row = 0, part_rows = 0, out_row = 0;
+  uint64_t row = 0;                // resident row of point 0 (accumulator slot and result row of point i: row + i)
   uint64_t remaining = 0;          // trees not yet walked
   int64_t points_left = 0;
   bool admitted = false, finished = false, cancelled = false;
@@ -125,8 +129,6 @@ struct Unit {
   uint32_t first, cnt;
 };
 
-uint32_t point_chunks(uint32_t N) { return N == 0 ? 1u : (N + grt::kBinChunk - 1) / grt::kBinChunk; }
-
 }  // namespace
 
 struct grt_server {
@@ -135,10 +137,10 @@ struct grt_server {
   uint64_t budget = 0, step_trees = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t streams[kStreams] = {};
-  grt::DevBuf part_pool, out_u, out_coef, out_se, out_status;
-  RowPool part_rows, out_rows;
-  grt::DevBuf rec_w, rec_o, meta, xbuf, work, cmeta;
-  size_t meta_points = 0;
+  grt::DevBuf acc_pool, out_u, out_coef, out_se, out_status;
+  RowPool rows;  // resident point rows
+  grt::DevBuf rec_w, rec_o, meta, xbuf, work, cmeta, step_part;
+  size_t meta_points = 0, part_slots = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request *> pending;
@@ -163,9 +165,29 @@ struct grt_server {
 
 namespace {
 
+// Step buffers of a server whose steps take at most step_trees trees: records (8 + 1 bytes per tree
+// slot, 4-aligned per point), per-point arrays of up to 2 mp + 1 entries (a group's arrays hold
+// n + 1 entries), coordinates, work counters per group, and the step's chunk sums (a unit of c trees
+// makes ceil(c / 8192) chunks, at least one, so a step makes at most step_trees / 8192 + mp).
+struct StepSizes {
+  size_t mp, meta_bytes, xbuf_bytes, work_bytes, rec_slots, part_slots, step_bytes;
+};
+StepSizes step_sizes(uint64_t step_trees) {
+  StepSizes z;
+  z.mp = (size_t)std::min<uint64_t>(1ull << 20, std::max<uint64_t>(4096, step_trees / 256));
+  z.meta_bytes = 10 * (2 * z.mp + 1) * sizeof(uint32_t);
+  z.xbuf_bytes = 2 * z.mp * (GRT_MAX_DIM + 1) * sizeof(double);
+  z.work_bytes = 132 * z.mp + 64;
+  z.rec_slots = (size_t)step_trees + 4 * z.mp + 64;
+  z.part_slots = (size_t)(step_trees / grt::kBinChunk) + z.mp + 1;
+  z.step_bytes = z.rec_slots * 9 + z.meta_bytes + z.xbuf_bytes + z.work_bytes + z.part_slots * kPartStride * 8 +
+                 64 * 1024;
+  return z;
+}
+
 // Per-point launch arrays of one group, laid out in one host block and copied once.
 struct GroupMeta {
-  std::vector<uint32_t> ntrees, prefix, tree_first, point_id, ntotal, part_slot, out_slot, chunk_prefix;
+  std::vector<uint32_t> ntrees, prefix, tree_first, point_id, ntotal, out_slot, chunk_prefix;
   std::vector<unsigned long long> tree_prefix;
   std::vector<double> x, t;
 };
@@ -183,17 +205,17 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     return a->seed < b->seed;
   };
   std::stable_sort(units.begin(), units.end(), [&](const Unit &a, const Unit &b) { return key_less(a.r, b.r); });
-  // every group gets disjoint regions of the step buffers (points, records, work counters), so the
-  // groups run concurrently on the server's streams
+  // every group gets disjoint regions of the step buffers (points, records, chunk sums, work
+  // counters), so the groups run concurrently on the server's streams
   const size_t u32n = (2 * meta_points + 1) * sizeof(uint32_t);  // entries of one per-point array
   unsigned char *mb = meta.as<unsigned char>();
   uint32_t *a_ntrees = reinterpret_cast<uint32_t *>(mb + 0 * u32n), *a_prefix = reinterpret_cast<uint32_t *>(mb + 1 * u32n),
            *a_first = reinterpret_cast<uint32_t *>(mb + 2 * u32n), *a_pid = reinterpret_cast<uint32_t *>(mb + 3 * u32n),
-           *a_ntot = reinterpret_cast<uint32_t *>(mb + 4 * u32n), *a_pslot = reinterpret_cast<uint32_t *>(mb + 5 * u32n),
-           *a_oslot = reinterpret_cast<uint32_t *>(mb + 6 * u32n), *a_cpre = reinterpret_cast<uint32_t *>(mb + 7 * u32n);
+           *a_ntot = reinterpret_cast<uint32_t *>(mb + 4 * u32n), *a_oslot = reinterpret_cast<uint32_t *>(mb + 5 * u32n),
+           *a_cpre = reinterpret_cast<uint32_t *>(mb + 6 * u32n);
   unsigned long long *a_tpre = reinterpret_cast<unsigned long long *>(mb + 8 * u32n);
   double *a_x = xbuf.as<double>(), *a_t = a_x + 2 * meta_points * GRT_MAX_DIM;
-  size_t pt_off = 0, rec_off = 0, work_off = 0;
+  size_t pt_off = 0, rec_off = 0, work_off = 0, part_off = 0;
   int gidx = 0;
   size_t g0 = 0;
   while (g0 < units.size()) {
@@ -209,7 +231,6 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     m.tree_first.resize(n);
     m.point_id.resize(n);
     m.ntotal.resize(n);
-    m.part_slot.resize(n);
     m.out_slot.resize(n);
     m.chunk_prefix.resize(n + 1);
     m.tree_prefix.resize(n + 1);
@@ -232,8 +253,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
       m.tree_first[k] = u.first;
       m.point_id[k] = (uint32_t)(r.point_base + (uint64_t)u.i);
       m.ntotal[k] = r.N[u.i];
-      m.part_slot[k] = r.part_slot[u.i];
-      m.out_slot[k] = (uint32_t)(r.out_row + (uint64_t)u.i);
+      m.out_slot[k] = (uint32_t)(r.row + (uint64_t)u.i);
       for (int d = 0; d < dim; ++d) m.x[k * dim + d] = r.x[(size_t)u.i * dim + d];
       m.t[k] = r.t[u.i];
       items += (u.cnt + grt::kTile - 1) / grt::kTile;
@@ -254,14 +274,15 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     }
     const size_t work_bytes = (64 + n * sizeof(uint32_t) + 63) & ~(size_t)63;
     if (pt_off + n + 1 > 2 * meta_points + 1 || (rec_off + recs) * 8 > rec_w.cap ||
-        rec_off + recs > rec_o.cap || work_off + work_bytes > work.cap) {
+        rec_off + recs > rec_o.cap || work_off + work_bytes > work.cap || part_off + chunks > part_slots) {
       why = "step larger than the server's step buffers";
       return GRT_EINVAL;
     }
     cudaStream_t st = streams[gidx % kStreams];
     uint32_t *d_ntrees = a_ntrees + pt_off, *d_prefix = a_prefix + pt_off, *d_first = a_first + pt_off,
-             *d_pid = a_pid + pt_off, *d_ntot = a_ntot + pt_off, *d_pslot = a_pslot + pt_off,
-             *d_oslot = a_oslot + pt_off, *d_cpre = a_cpre + pt_off;
+             *d_pid = a_pid + pt_off, *d_ntot = a_ntot + pt_off, *d_oslot = a_oslot + pt_off,
+             *d_cpre = a_cpre + pt_off;
+    double *d_part = step_part.as<double>() + part_off * kPartStride;
     unsigned long long *d_tpre = a_tpre + pt_off;
     double *d_x = a_x + pt_off * GRT_MAX_DIM, *d_t = a_t + pt_off;
     unsigned char *d_work = work.as<unsigned char>() + work_off;
@@ -276,7 +297,6 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     cp(d_first, m.tree_first.data(), n * 4);
     cp(d_pid, m.point_id.data(), n * 4);
     cp(d_ntot, m.ntotal.data(), n * 4);
-    cp(d_pslot, m.part_slot.data(), n * 4);
     cp(d_oslot, m.out_slot.data(), n * 4);
     cp(d_cpre, m.chunk_prefix.data(), (n + 1) * 4);
     cp(d_tpre, m.tree_prefix.data(), (n + 1) * 8);
@@ -316,6 +336,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
       e = grt::launch_walk(fp64, dim, c->pb.strategy, w, grt::WalkConfig{}, num_sms, st);
       ++launches;
     }
+    // the group's chunk sums, in the step's chunk-sum buffer at the group's chunk numbering
     grt::FinalizeParams f{};
     f.rec_w = d_recw;
     f.rec_o = d_reco;
@@ -323,34 +344,35 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     f.ntrees = d_ntrees;
     f.chunk_prefix = d_cpre;
     f.total_chunks = (uint32_t)chunks;
-    f.part = part_pool.as<double>();
-    f.tree_first = d_first;
-    f.part_slot = d_pslot;
+    f.part = d_part;
     f.part_stride = kPartStride;
     f.n = (int)n;
     f.K = K;
     f.stats = w.stats;
     if (e == cudaSuccess) e = grt::launch_finalize(fp64, f, st);
     ++launches;
-    // points whose last range was in this group: chunk sums -> a_n, SE_n, Pade
-    grt::CompleteParams cpl{};
-    cpl.n = (int)n;
-    cpl.K = K;
-    cpl.L = r0->L;
-    cpl.M = r0->M;
-    cpl.part = part_pool.as<double>();
-    cpl.part_stride = kPartStride;
-    cpl.part_slot = d_pslot;
-    cpl.ntrees = d_ntrees;
-    cpl.ntotal = d_ntot;
-    cpl.tree_first = d_first;
-    cpl.out_slot = d_oslot;
-    cpl.out_stride = kOutStride;
-    cpl.u = out_u.as<double>();
-    cpl.coef = out_coef.as<double>();
-    cpl.se = out_se.as<double>();
-    cpl.status = out_status.as<int32_t>();
-    if (e == cudaSuccess) e = grt::launch_complete(cpl, st);
+    // each unit's chunk sums into its point's accumulator; points whose last range this is:
+    // a_n, SE_n, Pade
+    grt::FoldParams fo{};
+    fo.n = (int)n;
+    fo.K = K;
+    fo.L = r0->L;
+    fo.M = r0->M;
+    fo.part = d_part;
+    fo.part_stride = kPartStride;
+    fo.chunk_prefix = d_cpre;
+    fo.acc = acc_pool.as<double>();
+    fo.acc_stride = kAccStride;
+    fo.slot = d_oslot;
+    fo.tree_first = d_first;
+    fo.ntrees = d_ntrees;
+    fo.ntotal = d_ntot;
+    fo.out_stride = kOutStride;
+    fo.u = out_u.as<double>();
+    fo.coef = out_coef.as<double>();
+    fo.se = out_se.as<double>();
+    fo.status = out_status.as<int32_t>();
+    if (e == cudaSuccess) e = grt::launch_fold(fo, st);
     ++launches;
     if (e != cudaSuccess) {
       why = std::string("step launch: ") + cudaGetErrorString(e);
@@ -359,6 +381,7 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
     pt_off += n + 1;
     rec_off += recs;
     work_off += work_bytes;
+    part_off += chunks;
     ++gidx;
     g0 = g1;
   }
@@ -372,7 +395,8 @@ int grt_server::run_step(std::vector<Unit> &units, std::string &why) {
   return GRT_OK;
 }
 
-// Completion of the unfinished points of cancelled requests from the chunks binned so far.
+// Completion of the unfinished points of cancelled requests from their accumulators (the chunks
+// binned so far: N_done trees, where a point whose first range never ran has zero sums).
 int grt_server::complete_cancelled(const std::vector<Request *> &reqs, std::string &why) {
   // one completion launch per series shape (K, L, M); points of one request share it
   std::map<std::tuple<int, int, int>, std::vector<std::pair<Request *, int64_t>>> by_shape;
@@ -382,36 +406,36 @@ int grt_server::complete_cancelled(const std::vector<Request *> &reqs, std::stri
   for (auto &kv : by_shape) {
     const auto &pts = kv.second;
     const size_t n = pts.size();
-    std::vector<uint32_t> h((size_t)4 * n);  // part slot, chunks, trees, output row
+    std::vector<uint32_t> h((size_t)3 * n);  // slot, trees so far (= N_done), trees of this "range" (none)
     for (size_t k = 0; k < n; ++k) {
       const Request *r = pts[k].first;
       const int64_t i = pts[k].second;
-      h[k] = r->part_slot[i];
-      h[n + k] = r->done[i] / grt::kBinChunk;  // an unfinished point's ranges end on chunk boundaries
-      h[2 * n + k] = r->done[i];
-      h[3 * n + k] = (uint32_t)(r->out_row + (uint64_t)i);
+      h[k] = (uint32_t)(r->row + (uint64_t)i);
+      h[n + k] = r->done[i];  // an unfinished point's ranges end on chunk boundaries
+      h[2 * n + k] = 0u;
     }
     cudaError_t e = cmeta.ensure(h.size() * sizeof(uint32_t));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(cmeta.ptr, h.data(), h.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, streams[0]);
-    grt::CompleteParams cp{};
-    cp.n = (int)n;
-    cp.K = std::get<0>(kv.first);
-    cp.L = std::get<1>(kv.first);
-    cp.M = std::get<2>(kv.first);
-    cp.part = part_pool.as<double>();
-    cp.part_stride = kPartStride;
-    cp.part_slot = cmeta.as<uint32_t>();
-    cp.nchunks = cp.part_slot + n;
-    cp.ntrees = cp.part_slot + 2 * n;
-    cp.out_slot = cp.part_slot + 3 * n;
-    cp.out_stride = kOutStride;
-    cp.u = out_u.as<double>();
-    cp.coef = out_coef.as<double>();
-    cp.se = out_se.as<double>();
-    cp.status = out_status.as<int32_t>();
-    cp.extra_status = GRT_STATUS_SERIES_PARTIAL;
-    if (e == cudaSuccess) e = grt::launch_complete(cp, streams[0]);
+    grt::FoldParams fo{};
+    fo.n = (int)n;
+    fo.K = std::get<0>(kv.first);
+    fo.L = std::get<1>(kv.first);
+    fo.M = std::get<2>(kv.first);
+    fo.part = nullptr;  // no chunk sums to add: complete from the accumulator with N = N_done
+    fo.acc = acc_pool.as<double>();
+    fo.acc_stride = kAccStride;
+    fo.slot = cmeta.as<uint32_t>();
+    fo.tree_first = fo.slot + n;
+    fo.ntrees = fo.slot + 2 * n;
+    fo.ntotal = fo.tree_first;
+    fo.out_stride = kOutStride;
+    fo.u = out_u.as<double>();
+    fo.coef = out_coef.as<double>();
+    fo.se = out_se.as<double>();
+    fo.status = out_status.as<int32_t>();
+    fo.extra_status = GRT_STATUS_SERIES_PARTIAL;
+    if (e == cudaSuccess) e = grt::launch_fold(fo, streams[0]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(streams[0]);
     ++launches;
     if (e != cudaSuccess) {
@@ -450,21 +474,20 @@ void grt_server::run() {
       r->status.resize(n);
       r->coef.resize(n * K1);
       r->se.resize(n * K1);
-      cudaError_t e = cudaMemcpy(r->u.data(), out_u.as<double>() + r->out_row, n * 8, cudaMemcpyDeviceToHost);
+      cudaError_t e = cudaMemcpy(r->u.data(), out_u.as<double>() + r->row, n * 8, cudaMemcpyDeviceToHost);
       if (e == cudaSuccess)
-        e = cudaMemcpy(r->status.data(), out_status.as<int32_t>() + r->out_row, n * 4, cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(r->status.data(), out_status.as<int32_t>() + r->row, n * 4, cudaMemcpyDeviceToHost);
       if (e == cudaSuccess)
-        e = cudaMemcpy2D(r->coef.data(), K1 * 8, out_coef.as<double>() + r->out_row * kOutStride, kOutStride * 8, K1 * 8,
+        e = cudaMemcpy2D(r->coef.data(), K1 * 8, out_coef.as<double>() + r->row * kOutStride, kOutStride * 8, K1 * 8,
                          n, cudaMemcpyDeviceToHost);
       if (e == cudaSuccess)
-        e = cudaMemcpy2D(r->se.data(), K1 * 8, out_se.as<double>() + r->out_row * kOutStride, kOutStride * 8, K1 * 8, n,
+        e = cudaMemcpy2D(r->se.data(), K1 * 8, out_se.as<double>() + r->row * kOutStride, kOutStride * 8, K1 * 8, n,
                          cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
         r->error = GRT_EDEVICE;
         r->error_text = cudaGetErrorString(e);
       }
-      part_rows.release(r->part_row, r->part_rows);
-      out_rows.release(r->out_row, (uint64_t)r->n);
+      rows.release(r->row, (uint64_t)r->n);
       r->finished = true;
       r->t_finish = Clock::now();
       active.erase(active.begin() + (ptrdiff_t)k);
@@ -475,24 +498,14 @@ void grt_server::run() {
     // admission: first come, first admitted, while the resident state fits the budget
     while (!pending.empty()) {
       Request *r = pending.front();
-      uint64_t prow = 0, orow = 0;
-      if (!part_rows.alloc(r->part_rows, &prow)) break;
-      if (!out_rows.alloc((uint64_t)r->n, &orow)) {
-        part_rows.release(prow, r->part_rows);
-        break;
-      }
-      r->part_row = prow;
-      r->out_row = orow;
-      uint64_t slot = prow;
-      for (int64_t i = 0; i < r->n; ++i) {
-        r->part_slot[i] = (uint32_t)slot;
-        slot += point_chunks(r->N[i]);
-      }
+      uint64_t row = 0;
+      if (!rows.alloc((uint64_t)r->n, &row)) break;
+      r->row = row;
       r->admitted = true;
       pending.pop_front();
       active.push_back(r);
     }
-    // cancelled requests: their unfinished points are completed from the chunks binned so far
+    // cancelled requests: their unfinished points are completed from the trees binned so far
     std::vector<Request *> canc;
     for (Request *r : active)
       if (r->cancelled && r->points_left > 0) canc.push_back(r);
@@ -576,7 +589,8 @@ void grt_server::run() {
 extern "C" {
 
 void grt_server::release_buffers() {
-  part_pool.release();
+  acc_pool.release();
+  step_part.release();
   out_u.release();
   out_status.release();
   out_coef.release();
@@ -595,6 +609,14 @@ void grt_server::release_buffers() {
   stream = nullptr;
 }
 
+int grt_server_sizes(uint64_t step_trees, uint64_t *step_bytes, uint64_t *point_bytes) {
+  if (step_trees == 0) step_trees = 1ull << 27;
+  if (step_trees < (uint64_t)grt::kBinChunk || step_trees > (1ull << 31)) return GRT_EINVAL;
+  if (step_bytes) *step_bytes = step_sizes(step_trees).step_bytes;
+  if (point_bytes) *point_bytes = kPointBytes;
+  return GRT_OK;
+}
+
 int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees, grt_server **out) {
   if (!out) return GRT_EINVAL;
   *out = nullptr;
@@ -607,44 +629,36 @@ int grt_server_create(int device, uint64_t mem_budget_bytes, uint64_t step_trees
   s->device = device;
   s->budget = mem_budget_bytes;
   s->step_trees = step_trees;
-  s->meta_points = (size_t)std::min<uint64_t>(1ull << 20, std::max<uint64_t>(4096, step_trees / 256));
-  const size_t mp = s->meta_points;
-  // step buffers: records (8 + 1 bytes per tree slot, 4-aligned per point), per-point arrays of up
-  // to 2 mp + 1 entries (a group's arrays hold n + 1 entries), coordinates, work counters per group
-  const size_t meta_bytes = 10 * (2 * mp + 1) * sizeof(uint32_t);
-  const size_t xbuf_bytes = 2 * mp * (GRT_MAX_DIM + 1) * sizeof(double);
-  const size_t work_bytes = 132 * mp + 64;
-  const size_t rec_slots = (size_t)step_trees + 4 * mp + 64;
-  const size_t step_bytes = rec_slots * 9 + meta_bytes + xbuf_bytes + work_bytes + 64 * 1024;
-  if (mem_budget_bytes < step_bytes + (1ull << 20)) {
+  const StepSizes z = step_sizes(step_trees);
+  s->meta_points = z.mp;
+  s->part_slots = z.part_slots;
+  if (mem_budget_bytes < z.step_bytes + (1ull << 20)) {
     delete s;
     return GRT_EINVAL;  // the budget must hold the step buffers and some resident state
   }
-  const uint64_t resident = mem_budget_bytes - step_bytes;
-  const uint64_t part_cap = (resident * 3 / 4) / (kPartStride * 8);
-  const uint64_t out_cap = (resident / 4) / ((2 * kOutStride + 2) * 8);
+  const uint64_t cap = std::min<uint64_t>((mem_budget_bytes - z.step_bytes) / kPointBytes, 1ull << 31);  // points
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
   for (int k = 0; k < kStreams && e == cudaSuccess; ++k)
     e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = s->part_pool.ensure(part_cap * kPartStride * 8);
-  if (e == cudaSuccess) e = s->out_u.ensure(out_cap * 8);
-  if (e == cudaSuccess) e = s->out_status.ensure(out_cap * 4);
-  if (e == cudaSuccess) e = s->out_coef.ensure(out_cap * kOutStride * 8);
-  if (e == cudaSuccess) e = s->out_se.ensure(out_cap * kOutStride * 8);
-  if (e == cudaSuccess) e = s->rec_w.ensure(rec_slots * 8);
-  if (e == cudaSuccess) e = s->rec_o.ensure(rec_slots);
-  if (e == cudaSuccess) e = s->meta.ensure(meta_bytes);
-  if (e == cudaSuccess) e = s->xbuf.ensure(xbuf_bytes);
-  if (e == cudaSuccess) e = s->work.ensure(work_bytes);
+  if (e == cudaSuccess) e = s->acc_pool.ensure(cap * kAccStride * 8);
+  if (e == cudaSuccess) e = s->out_u.ensure(cap * 8);
+  if (e == cudaSuccess) e = s->out_status.ensure(cap * 4);
+  if (e == cudaSuccess) e = s->out_coef.ensure(cap * kOutStride * 8);
+  if (e == cudaSuccess) e = s->out_se.ensure(cap * kOutStride * 8);
+  if (e == cudaSuccess) e = s->rec_w.ensure(z.rec_slots * 8);
+  if (e == cudaSuccess) e = s->rec_o.ensure(z.rec_slots);
+  if (e == cudaSuccess) e = s->meta.ensure(z.meta_bytes);
+  if (e == cudaSuccess) e = s->xbuf.ensure(z.xbuf_bytes);
+  if (e == cudaSuccess) e = s->work.ensure(z.work_bytes);
+  if (e == cudaSuccess) e = s->step_part.ensure(z.part_slots * kPartStride * 8);
   if (e != cudaSuccess) {
     s->release_buffers();
     delete s;
     return e == cudaErrorMemoryAllocation ? GRT_ENOMEM : GRT_EDEVICE;
   }
   s->stream = s->streams[0];
-  s->part_rows.init(part_cap);
-  s->out_rows.init(out_cap);
+  s->rows.init(cap);
   s->worker = std::thread([s]() { s->run(); });
   *out = s;
   return GRT_OK;
@@ -691,7 +705,6 @@ int grt_submit(grt_server *s, grt_ctx *c, int64_t n, const double *x, const doub
   r->N.resize(n);
   r->done.assign(n, 0);
   r->complete.assign(n, 0);
-  r->part_slot.assign(n, 0);
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT || !std::isfinite(t[i]) || t[i] < 0.0) {
       delete r;
@@ -699,7 +712,6 @@ int grt_submit(grt_server *s, grt_ctx *c, int64_t n, const double *x, const doub
     }
     r->N[i] = (uint32_t)ntrees[i];
     r->remaining += ntrees[i];
-    r->part_rows += point_chunks(r->N[i]);
   }
   r->points_left = n;
   r->t_submit = Clock::now();
@@ -709,7 +721,7 @@ int grt_submit(grt_server *s, grt_ctx *c, int64_t n, const double *x, const doub
       delete r;
       return s->set_error(s->fatal, "server stopped after a device error: " + s->err);
     }
-    if (r->part_rows > s->part_rows.capacity() || (uint64_t)n > s->out_rows.capacity()) {
+    if ((uint64_t)n > s->rows.capacity()) {
       delete r;
       return s->set_error(GRT_ENOMEM, "request larger than the server's memory budget");
     }
@@ -814,7 +826,7 @@ int grt_server_stats(grt_server *s, uint64_t *steps, uint64_t *trees, uint64_t *
   if (trees) *trees = s->trees_walked;
   if (launches) *launches = s->launches;
   if (resident_bytes)
-    *resident_bytes = s->part_rows.used() * kPartStride * 8 + s->out_rows.used() * (2 * kOutStride + 2) * 8;
+    *resident_bytes = s->rows.used() * kPointBytes;
   if (pending_requests) *pending_requests = s->pending.size();
   if (active_requests) *active_requests = s->active.size();
   if (shared_launches) *shared_launches = s->shared_launches;

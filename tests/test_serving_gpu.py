@@ -89,20 +89,28 @@ def test_results_equal_one_shot_solves_in_a_concurrent_mix(grt):
         c.close()
 
 
+def _min_budget(grt, step):
+    """The smallest budget a server with this step size accepts, and the points it holds resident."""
+    sz = grt.grt_server_sizes(step)
+    return sz["step_bytes"] + (1 << 20), (1 << 20) // sz["point_bytes"]
+
+
 def test_admission_waits_for_memory(grt):
     wl = workloads.workload_sin_2d()
     ctx = grt.grt_create(wl["problem"], 0)
-    # resident part of the budget: 1 MB = ~1365 chunk rows of 8192 trees; each request below
-    # needs 20 points x 20 chunks = 400 rows, so at most three are admitted at a time
     step = 1 << 16
-    P = 4096
-    budget = 9 * (step + 4 * P + 64) + 312 * P + 66 * 1024 + (1 << 20)
+    budget, cap = _min_budget(grt, step)
+    # each request below has 200 points, each point one resident accumulator and result row: at most
+    # three requests are admitted at a time
+    assert 600 <= cap < 800
     server = grt.grt_server_create(0, mem_budget_bytes=budget, step_trees=step)
-    nt = np.full(20, 20 * 8192, np.uint64)
+    rng = np.random.default_rng(5)
+    x, t = rng.uniform(-3.0, 3.0, (2400, 2)), rng.uniform(0.1, 1.0, 2400)
+    nt = np.full(200, 20 * 8192, np.uint64)
     ids = []
     for k in range(12):
-        sl = slice(k * 20, k * 20 + 20)
-        ids.append(grt.grt_submit(server, ctx, wl["x"][sl], wl["t"][sl], nt, wl["K"], wl["L"], wl["M"], 0, k * 20))
+        sl = slice(k * 200, k * 200 + 200)
+        ids.append(grt.grt_submit(server, ctx, x[sl], t[sl], nt, wl["K"], wl["L"], wl["M"], 0, k * 200))
     peak_active = 0
     res = {}
     while len(res) < len(ids):
@@ -114,8 +122,7 @@ def test_admission_waits_for_memory(grt):
                 if r is not None:
                     res[rid] = r
     assert 1 <= peak_active <= 3
-    ref = grt.grt_solve(ctx, wl["x"][:240], wl["t"][:240], np.full(240, 20 * 8192, np.uint64), wl["K"], wl["L"],
-                        wl["M"], 0)
+    ref = grt.grt_solve(ctx, x, t, np.full(2400, 20 * 8192, np.uint64), wl["K"], wl["L"], wl["M"], 0)
     assert np.array_equal(np.concatenate([res[rid]["coef"] for rid in ids]), ref["coef"])
     server.close()
     ctx.close()
@@ -126,15 +133,17 @@ def test_errors_and_empty_requests(grt):
     ctx = grt.grt_create(wl["problem"], 0)
     with pytest.raises(grt.GrtError):
         grt.grt_server_create(0, mem_budget_bytes=1 << 20, step_trees=1 << 16)  # budget below the step buffers
-    # 64 MB: ~86K resident chunk rows; a point of 2^31 - 1 trees needs 262144
-    server = grt.grt_server_create(0, mem_budget_bytes=64 << 20, step_trees=1 << 16)
+    budget, cap = _min_budget(grt, 1 << 16)
+    server = grt.grt_server_create(0, mem_budget_bytes=budget, step_trees=1 << 16)
     rid = grt.grt_submit(server, ctx, np.zeros((0, 2)), np.zeros(0), np.zeros(0, np.uint64), 10, 5, 5, 0)
     r = grt.grt_poll(server, rid, 0)
     assert r is not None and r["u"].shape == (0,)
     with pytest.raises(grt.GrtError):
         grt.grt_submit(server, ctx, np.zeros((1, 2)), [1.0], [10], 10, 6, 5, 0)
-    with pytest.raises(grt.GrtError):  # more resident state than the whole budget
-        grt.grt_submit(server, ctx, np.zeros((1, 2)), [1.0], [2**31 - 1], 10, 5, 5, 0)
+    with pytest.raises(grt.GrtError):  # more points than the whole budget holds resident
+        grt.grt_submit(server, ctx, np.zeros((cap + 1, 2)), np.ones(cap + 1), np.ones(cap + 1, np.uint64), 10, 5, 5, 0)
+    with pytest.raises(grt.GrtError):
+        grt.grt_server_sizes(4096)  # steps below one 8192-tree chunk
     rid = grt.grt_submit(server, ctx, np.zeros((3, 2)), [0.5, 1.0, 0.25], [20000, 1, 0], 10, 5, 5, 7)
     assert grt.grt_poll(server, rid, -1)["u"].shape == (3,)
     server.close()
@@ -180,14 +189,16 @@ def test_cancelled_request_ends_with_the_trees_binned_so_far(grt):
     ctx = grt.grt_create(wl["problem"], 0)
     K, L, M = wl["K"], wl["L"], wl["M"]
     step = 1 << 16
-    P = 4096
-    budget = 9 * (step + 4 * P + 64) + 312 * P + 66 * 1024 + (1 << 20)  # ~1558 resident chunk rows
+    budget, cap = _min_budget(grt, step)
     server = grt.grt_server_create(0, mem_budget_bytes=budget, step_trees=step)
     nt = np.array([8 * 8192 + 5, 300_000, 1000, 500_000, 2 * 8192, 777_777], np.uint64)
     x, t = wl["x"][100:106], wl["t"][100:106]
     rid = grt.grt_submit(server, ctx, x, t, nt, K, L, M, 9, 100)
-    # a second request needing more resident rows than are left waits for admission
-    waiting = grt.grt_submit(server, ctx, wl["x"][:2], wl["t"][:2], np.full(2, 700 * 8192, np.uint64), K, L, M, 9, 0)
+    # a second request with more points than the budget has rows left waits for admission
+    nw = cap - len(nt) + 1
+    rng = np.random.default_rng(3)
+    waiting = grt.grt_submit(server, ctx, rng.uniform(-3.0, 3.0, (nw, 2)), rng.uniform(0.1, 1.0, nw),
+                             np.full(nw, 8192, np.uint64), K, L, M, 9, 1000)
     t0 = time.time()
     while grt.grt_server_stats(server)["steps"] < 4 and time.time() - t0 < 30:
         time.sleep(0.0005)
@@ -217,6 +228,6 @@ def test_cancelled_request_ends_with_the_trees_binned_so_far(grt):
         _assert_fp32_parity(gi, o, nd[i:i + 1], L=L, M=M)
     assert np.all(w["ntrees_done"] == 0) and np.all(w["u"] == 0.0) and np.all(w["coef"] == 0.0)
     assert np.all(w["status"] & grt.STATUS_SERIES_PARTIAL)
-    zero = grt.grt_solve(ctx, wl["x"][:2], wl["t"][:2], np.zeros(2, np.uint64), K, L, M, 9, 0)
-    assert np.array_equal(w["status"] & ~grt.STATUS_SERIES_PARTIAL, zero["status"])
+    zero = grt.grt_solve(ctx, wl["x"][:1], wl["t"][:1], np.zeros(1, np.uint64), K, L, M, 9, 0)
+    assert np.all((w["status"] & ~grt.STATUS_SERIES_PARTIAL) == zero["status"][0])
     ctx.close()
