@@ -407,6 +407,47 @@ def test_full_size_sin_2d_every_point(grt):
     assert np.max(np.abs(g["u"] - o["u"]) / scale) <= 1e-5
 
 
+def test_largest_budgets(grt):
+    """Three sin_2d points of the largest budget, GRT_MAX_TREES_PER_POINT = 2^31 - 1 trees each:
+    6.4e9 tree records, more slots than one walk launch addresses (2^32), so the solve runs as
+    several walk launches.  Each point's result is that of its own solve, bit for bit, and that of
+    the server, which walks it in steps of 2^27 trees and folds the chunk sums into the point's
+    accumulator across them.  Against the FP64 oracle over the first 10^6 trees of each point's
+    stream (an independent estimate up to those shared trees): every well-sampled coefficient
+    within 5 of the oracle's standard errors (plus the FP32 bar), the Pade value within 5 of the
+    oracle's first-order Pade error."""
+    wl = workloads.workload_sin_2d()
+    K, L, M, seed = wl["K"], wl["L"], wl["M"], wl["seed"]
+    idx = np.array([40, 135, 400])
+    x, t = wl["x"][idx], wl["t"][idx]
+    big = np.full(3, 2**31 - 1, np.uint64)
+    ctx = grt.grt_create(wl["problem"], 0)
+    g = grt.grt_solve(ctx, x, t, big, K, L, M, seed, 1000)
+    for i in range(3):
+        alone = grt.grt_solve(ctx, x[i:i + 1], t[i:i + 1], big[i:i + 1], K, L, M, seed, 1000 + i)
+        assert np.array_equal(alone["coef"][0], g["coef"][i]) and np.array_equal(alone["se"][0], g["se"][i])
+        assert alone["u"][0] == g["u"][i] and alone["status"][0] == g["status"][i]
+    sz = grt.grt_server_sizes(0)
+    server = grt.grt_server_create(0, mem_budget_bytes=sz["step_bytes"] + (64 << 20), step_trees=0)
+    rid = grt.grt_submit(server, ctx, x, t, big, K, L, M, seed, 1000)
+    r = grt.grt_poll_ex(server, rid, -1)
+    steps = grt.grt_server_stats(server)["steps"]
+    server.close()
+    ctx.close()
+    assert steps >= 48 and np.array_equal(r["ntrees_done"], big)  # steps of at most 2^27 trees
+    for k in ("coef", "se", "status"):
+        assert np.array_equal(r[k], g[k]), k
+    assert np.array_equal(r["u"], g["u"])
+    n0 = np.full(3, 10**6, np.uint64)
+    o = oracle.solve(wl["problem"], x, t, n0, K, L, M, seed, point_base=1000)
+    well = o["cnt"][:, : K + 1] >= 1000
+    mean_abs = o["sa"] / np.maximum(o["cnt"][:, : K + 1].astype(float), 1.0)
+    dev = np.abs(g["coef"] - o["coef"])
+    assert np.all(dev[well] <= 5.0 * o["se"][well] + 3e-5 * mean_abs[well]), np.max(dev[well] / o["se"][well])
+    perr = oracle.pade_error(o["coef"], o["se"], L, M)
+    assert np.all(np.abs(g["u"] - o["u"]) <= 5.0 * perr + 1e-5 * np.abs(o["coef"]).sum(axis=1))
+
+
 def test_invalid_coefficient_profiles_rejected(grt):
     bad = [dict(workloads.problem_var_coef_2d(), coef=("gauss_over_t", (1, 0, 0, 0, 0, 0, 0.0), [2])),
            dict(workloads.problem_var_coef_2d("A"), f_coef=[0.0, 0.5, -1.0], c_pot=1.0,
