@@ -93,7 +93,9 @@ def _load():
         raise RuntimeError(f"libgrt.so is not built ({LIB_PATH}); run __graft_entry__.build()")
     lib = ctypes.CDLL(LIB_PATH)
     i64, u64, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
-    f64p, u64p, i32p, u32p = _P(ctypes.c_double), _P(ctypes.c_uint64), _P(ctypes.c_int32), _P(ctypes.c_uint32)
+    # host arrays go in as plain addresses (`_ptr`): an int converts to a void pointer far faster
+    # than a typed ctypes pointer is built (a per-call cost of the synchronous solves)
+    f64p = u64p = i32p = u32p = _vp
     sig = {
         "grt_create": ([_P(grt_problem), i32, _P(_vp)], i32),
         "grt_destroy": ([_vp], None),
@@ -145,7 +147,16 @@ def library_path() -> str:
 
 
 def _ptr(a, ctype):
-    return None if a is None else a.ctypes.data_as(_P(ctype))
+    """The address of a host array (ctype names its element type for the reader), None for None."""
+    return None if a is None else a.ctypes.data
+
+
+def _vec(a, dtype, n: int):
+    """a as a contiguous length-n array of dtype (a scalar is broadcast), without a copy when it
+    already is one."""
+    if isinstance(a, np.ndarray) and a.dtype == dtype and a.ndim == 1 and a.shape[0] == n and a.flags.c_contiguous:
+        return a
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype), (n,)))
 
 
 def _devptr(obj):
@@ -288,8 +299,8 @@ def grt_solve(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: int, poi
     d = ctx.dim
     xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
     n = xs.shape[0]
-    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
-    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    ts = _vec(t, np.float64, n)
+    nt = _vec(ntrees, np.uint64, n)
     if out is None:
         out = {}
     u = out.get("u")
@@ -318,8 +329,8 @@ def grt_solve_plain(ctx: Context, x, t, ntrees, K: int, L: int, M: int, seed: in
     d = ctx.dim
     xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
     n = xs.shape[0]
-    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
-    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    ts = _vec(t, np.float64, n)
+    nt = _vec(ntrees, np.uint64, n)
     u = np.empty(n, np.float64)
     coef = np.empty((n, K + 1), np.float64) if want_coef else None
     se = np.empty((n, K + 1), np.float64) if want_se else None
@@ -557,8 +568,8 @@ def grt_submit(server: Server, ctx: Context, x, t, ntrees, K: int, L: int, M: in
     d = ctx.dim
     xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, d)
     n = xs.shape[0]
-    ts = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (n,)))
-    nt = np.ascontiguousarray(np.broadcast_to(np.asarray(ntrees, np.uint64), (n,)))
+    ts = _vec(t, np.float64, n)
+    nt = _vec(ntrees, np.uint64, n)
     rid = ctypes.c_uint64(0)
     _check_server(lib.grt_submit(server.handle, ctx.handle, n, _ptr(xs, ctypes.c_double), _ptr(ts, ctypes.c_double),
                                  _ptr(nt, ctypes.c_uint64), K, L, M, int(seed), int(point_base),
