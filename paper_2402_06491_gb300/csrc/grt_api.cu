@@ -55,6 +55,8 @@ struct grt_plan {
   bool timing = false, timed_last = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   grt::WalkConfig cfg{};             // launch shape of the walk (autotuned or set)
+  uint32_t tile_small = 0;           // queue chunk of points small_from .. n-1 (0: none)
+  int64_t small_from = 0;
   // walk launches: points [group_pt[g], group_pt[g+1]), whose records span fewer than 2^32 slots
   // (one group unless the plan holds that many records)
   std::vector<int64_t> group_pt;
@@ -301,14 +303,31 @@ int plan_configure(grt_plan *p, int64_t n, const uint64_t *ntrees, int K, int L,
   std::vector<unsigned long long> tprefix((size_t)n + 1);
   std::vector<uint32_t> cprefix((size_t)n + 1);
   uint64_t items = 0, trees = 0, chunks = 0, recs = 0;  // recs: record slots, each point's segment 4-aligned
+  // the points at the end of the queue, about its last 1/32 of the trees (when that is at most 1/16
+  // of them), are cut into 64-tree chunks: a warp that finds the queue empty then waits only for
+  // short chunks of the others, at the cost of more chunk fetches on a small share of the trees
+  uint64_t all = 0;
+  for (int64_t i = 0; i < n; ++i) all += ntrees[i];
+  p->tile_small = 0;
+  p->small_from = n;
+  if (p->cfg.tile > 64 && n > 1) {
+    uint64_t tail = 0;
+    int64_t i = n;
+    while (i > 1 && tail < all / 32) tail += ntrees[--i];
+    if (tail <= all / 16) {
+      p->tile_small = 64;
+      p->small_from = i;
+    }
+  }
   for (int64_t i = 0; i < n; ++i) {
     if (ntrees[i] > GRT_MAX_TREES_PER_POINT) return c->set_error(GRT_EINVAL, "ntrees[i] above 2^31 - 1");
+    const uint64_t tl = (p->tile_small != 0 && i >= p->small_from) ? p->tile_small : p->cfg.tile;
     prefix[(size_t)i] = (uint32_t)items;
     tprefix[(size_t)i] = recs;
     recs += (ntrees[i] + 3) & ~(uint64_t)3;
     cprefix[(size_t)i] = (uint32_t)chunks;
     chunks += ntrees[i] == 0 ? 1 : (ntrees[i] + grt::kBinChunk - 1) / grt::kBinChunk;
-    items += (ntrees[i] + p->cfg.tile - 1) / p->cfg.tile;
+    items += (ntrees[i] + tl - 1) / tl;
     trees += ntrees[i];
     nt32[(size_t)i] = (uint32_t)ntrees[i];
     if (items >= 0xFFFFFFFFull) return c->set_error(GRT_EINVAL, "too many work items (total trees too large)");
@@ -387,6 +406,8 @@ int plan_execute(grt_plan *p, const double *d_x, const double *d_t, uint64_t see
   w.tree_prefix = p->tree_prefix.as<unsigned long long>();
   w.n = (int)p->n;
   w.tile = p->cfg.tile;
+  w.tile_small = p->tile_small;
+  w.small_from = (int)p->small_from;
   w.total_items = p->total_items;
   w.rec_w = p->rec_w.ptr;
   w.rec_o = p->rec_o.as<uint8_t>();

@@ -70,6 +70,8 @@ struct WalkParams {
   const uint32_t *point_id;    // [n] random-stream point index of each point, or null (point_base + p)
   int n;
   uint32_t tile;             // trees per queue chunk
+  uint32_t tile_small;       // trees per queue chunk of points small_from .. n-1 (0: every point uses tile)
+  int small_from;
   uint32_t total_items;      // queue chunks: this launch takes items item_base .. total_items - 1
   uint32_t item_base;
   unsigned long long rec_base;  // record slot of rec_w[0] / rec_o[0] (the pointers are offset by it):

@@ -8,8 +8,9 @@
 // 4 warps, stack in shared memory) and grt_trees.cu (the diagnostic kernel).
 #pragma once
 //
-// Work decomposition: point p's N_p trees are cut into queue chunks of kTile
-// consecutive trees (the last one ragged), numbered point by point
+// Work decomposition: point p's N_p trees are cut into queue chunks of `tile`
+// consecutive trees (the last one ragged; a plan cuts the points at the queue's
+// end into shorter chunks, `tile_small`), numbered point by point
 // (prefix[p] = first chunk of point p).  Persistent warps take chunks from
 // one global counter; inside a warp every lane walks one tree at a time,
 // depth-first, with an explicit stack in shared memory.  A lane whose tree
@@ -172,8 +173,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) walk_kernel(const WalkParams p)
           }
           const int pt = find_point(p.prefix, p.n, item, lane);
           const uint32_t N = __ldg(p.ntrees + pt);
-          c_next = (item - __ldg(p.prefix + pt)) * p.tile;
-          c_end = min(c_next + p.tile, N);
+          const uint32_t tl = (p.tile_small != 0u && pt >= p.small_from) ? p.tile_small : p.tile;
+          c_next = (item - __ldg(p.prefix + pt)) * tl;
+          c_end = min(c_next + tl, N);
           c_point = p.point_id ? __ldg(p.point_id + pt) : p.point_base + (uint32_t)pt;
           c_first = p.tree_first ? __ldg(p.tree_first + pt) : 0u;
           c_rec = (uint32_t)(__ldg(p.tree_prefix + pt) - p.rec_base);
