@@ -1,12 +1,12 @@
 """GPU parity: the CUDA path against the FP64 oracle on the same random streams.
 
-Bars (spec tolerance; the reading of it near u = 0 is documented):
+Bars (the 1e-5 relative parity bar; its reading near u = 0 is documented):
   * integer results (tree order Ne, node counts, topology hashes, pruned counts)
     bit-exact for Strategy B at any precision and for FP64 walks;
   * FP64 walks: coefficients and Pade values to 1e-12 relative (per-tree weights too, with an
     absolute floor of 1e-13 of the sample's largest weight for cancelling initial data);
   * FP32 walks: the Pade value within 1e-5 * max(|u|, sum_n |a_n|) (the
-    spec bar; the max() reading keeps it meaningful where u ~ 0), and a_n
+    parity bar; the max() reading keeps it meaningful where u ~ 0), and a_n
     within 3e-5 of the mean |tree weight| of its order: a tree weight is a
     product of up to ~3K factors, each within a few FP32 ulp, so it carries at
     most ~3e-5 relative error, and a coefficient is a mean of weights.
