@@ -102,3 +102,31 @@ def test_pdd_points_match_the_oracle_layout(lib):
     with pytest.raises(pkg.GrtError):
         pkg.grt_pdd_points(dict(dim=2, lo=[0.0, 0.0], hi=[1.0, 1.0], sub=[2, 2], cells=[4, 4], nodes=[3, 5], t_nodes=4,
                                 T=1.0, nsteps=4))
+
+
+def test_host_arrays_pass_in_place_or_as_contiguous_copies(lib):
+    # the binding hands the library plain addresses: an array that already has the layout is used in
+    # place, anything else (strided, another dtype, a scalar to broadcast) becomes a contiguous copy
+    from paper_2402_06491_gb300 import _binding as b
+
+    a = np.arange(6, dtype=np.float64)
+    assert b._vec(a, np.float64, 6) is a and b._ptr(a, ctypes.c_double) == a.ctypes.data
+    v = b._vec(a[::2], np.float64, 3)
+    assert v.flags.c_contiguous and np.array_equal(v, a[::2])
+    w = b._vec(a.astype(np.float32), np.float64, 6)
+    assert w.dtype == np.float64 and np.array_equal(w, a)
+    assert np.array_equal(b._vec(0.5, np.float64, 4), np.full(4, 0.5))
+    assert b._ptr(None, ctypes.c_double) is None
+
+
+def test_server_memory_sizes(lib):
+    # host-only: the step buffers grow with the step size, a point's resident state does not
+    import paper_2402_06491_gb300 as pkg
+
+    small, large = pkg.grt_server_sizes(1 << 16), pkg.grt_server_sizes(1 << 20)
+    assert small["point_bytes"] == large["point_bytes"] == 1436
+    assert large["step_bytes"] > small["step_bytes"] > 9 * (1 << 16)
+    assert pkg.grt_server_sizes(0) == pkg.grt_server_sizes(1 << 27)
+    for bad in (4096, (1 << 31) + 1):
+        with pytest.raises(pkg.GrtError):
+            pkg.grt_server_sizes(bad)
