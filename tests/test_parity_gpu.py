@@ -448,6 +448,65 @@ def test_largest_budgets(grt):
     assert np.all(np.abs(g["u"] - o["u"]) <= 5.0 * perr + 1e-5 * np.abs(o["coef"]).sum(axis=1))
 
 
+def pade_jacobian(a, L, M):
+    """d u / d a_n, n = 0..L+M, of the oracle's [L/M] Pade value at eps = 1, by central differences."""
+    a = np.asarray(a, float)
+    J = np.zeros(L + M + 1)
+    for n in range(L + M + 1):
+        h = 1e-6 * max(abs(a[n]), 1e-12 * np.abs(a).max(), 1e-300)
+        ap, am = a.copy(), a.copy()
+        ap[n] += h
+        am[n] -= h
+        J[n] = (oracle.pade(ap, L, M)[0] - oracle.pade(am, L, M)[0]) / (2 * h)
+    return J
+
+
+def test_full_size_pdd_3d_every_point(grt):
+    """Every one of pdd_3d's 9216 point solves at its full budget (1e5 trees, t = 1, [6/6]) in the
+    autotuned shape the benchmark times, against the oracle on the same streams.
+
+    The coefficients are compared on the scale of the series, |a_n - a_n^or| <= 1e-5 sum_m |a_m^or|
+    (the scale of the Pade value's bar): near the zero planes of prod tanh(x_i - 2) a tree's weight
+    carries the absolute error of its FP32 position, so the relative per-tree bound of the other
+    tests does not hold for the sparse high orders there.  The Pade value then meets the 1e-5 bar at
+    every point where the oracle's approximant is well conditioned: relative condition
+    sum_n |du/da_n| |a_n| / max(|u|, sum |a_n|) <= 10 (from the oracle's coefficients alone).  At the
+    other points (reading G10: the approximant amplifies coefficient perturbations more than
+    tenfold; the oracle flags none of them, |Q(1)| stays above 1e-8) the difference must lie within
+    twice the first-order bound of the coefficient bar, sum_n |du/da_n| 1e-5 sum |a|; they are
+    counted, and must stay a small minority."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.workload_pdd_3d()
+    n, K, L, M = wl["x"].shape[0], wl["K"], wl["L"], wl["M"]
+    dev = torch.device("cuda:0")
+    x, t = torch.from_numpy(wl["x"]).to(dev), torch.from_numpy(wl["t"]).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    coef = torch.empty((n, K + 1), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = grt.grt_create(wl["problem"], 0)
+    plan = grt.grt_plan_create(ctx, wl["ntrees"], K, L, M)
+    grt.grt_plan_autotune(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    grt.grt_plan_execute(plan, x, t, wl["seed"], 0, u, coef, None, st)
+    torch.cuda.synchronize()
+    gu, gc, gs = u.cpu().numpy(), coef.cpu().numpy(), st.cpu().numpy()
+    plan.close()
+    ctx.close()
+    o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], K, L, M, wl["seed"])
+    asum = np.abs(o["coef"]).sum(axis=1)
+    assert np.all(np.abs(gc - o["coef"]) <= 1e-5 * asum[:, None]), np.max(np.abs(gc - o["coef"]) / asum[:, None])
+    assert np.array_equal(gs & 8, o["status"] & 8)
+    scale = np.maximum(np.abs(o["u"]), asum)
+    du = np.abs(gu - o["u"])
+    J = np.array([pade_jacobian(o["coef"][i], L, M) for i in range(n)])
+    cond = (np.abs(J) * np.abs(o["coef"][:, : L + M + 1])).sum(axis=1) / scale
+    ill = (cond > 10.0) | ((o["status"] & 3) != 0)
+    well = ~ill
+    assert np.all(du[well] <= 1e-5 * scale[well]), np.max(du[well] / scale[well])
+    bound = np.abs(J).sum(axis=1) * 1e-5 * asum
+    assert np.all(du[ill] <= 2.0 * bound[ill]), np.max(du[ill] / bound[ill])
+    assert ill.sum() <= n // 20, int(ill.sum())
+
+
 def test_invalid_coefficient_profiles_rejected(grt):
     bad = [dict(workloads.problem_var_coef_2d(), coef=("gauss_over_t", (1, 0, 0, 0, 0, 0, 0.0), [2])),
            dict(workloads.problem_var_coef_2d("A"), f_coef=[0.0, 0.5, -1.0], c_pot=1.0,
@@ -501,12 +560,12 @@ def test_plan_kappa_matches_oracle_sums(grt, precision):
     assert np.allclose(kg[well], ko[well], rtol=3e-3 if precision == "fp32" else 1e-9)
 
 
-@pytest.mark.parametrize("name,ctol", [("uneven_2d", 3e-5), ("pdd_3d", 1.5e-4), ("var_coef_2d", 3e-5),
-                                       ("drift_2d", 3e-5)])
-def test_full_size_workloads_sampled_points(grt, name, ctol):
-    """Every other benchmark workload at its full size, through the device-resident plan with the
-    autotuned launch shape the benchmark times; sampled points (spread over the index range and
-    the largest budget) recomputed one by one by the oracle (same global index)."""
+@pytest.mark.parametrize("name,ctol", [("uneven_2d", 3e-5), ("var_coef_2d", 3e-5), ("drift_2d", 3e-5)])
+def test_full_size_workloads_every_point(grt, name, ctol):
+    """Every other benchmark workload but pdd_3d (its own test above) at its full size, through the
+    device-resident plan with the autotuned launch shape the benchmark times, every point against
+    the oracle on the same streams; var_coef_2d and drift_2d have no point that may escape the bar,
+    uneven_2d only those the oracle flags or that lie past blow-up."""
     torch = pytest.importorskip("torch")
     wl = workloads.WORKLOADS[name]()
     n, K = wl["x"].shape[0], wl["K"]
@@ -524,15 +583,10 @@ def test_full_size_workloads_sampled_points(grt, name, ctol):
     plan.close()
     ctx.close()
     assert np.all(np.isfinite(g["u"]))
-    idx = sorted({0, n // 3, n // 2, (2 * n) // 3, n - 1, int(np.argmax(wl["ntrees"]))})
-    for i in idx:
-        o = oracle.solve(wl["problem"], wl["x"][i:i + 1], wl["t"][i:i + 1], wl["ntrees"][i:i + 1], K, wl["L"],
-                         wl["M"], wl["seed"], point_base=i)
-        gi = {k: g[k][i:i + 1] for k in ("u", "coef", "status")}
-        pb_mask = wl["past_blowup"][i:i + 1] if "past_blowup" in wl else None
-        esc = _assert_fp32_parity(gi, o, wl["ntrees"][i:i + 1], ctol=ctol, L=wl["L"], M=wl["M"], unpinned=pb_mask)
-        if name in ("var_coef_2d", "drift_2d"):
-            assert esc == []
+    o = oracle.solve(wl["problem"], wl["x"], wl["t"], wl["ntrees"], K, wl["L"], wl["M"], wl["seed"])
+    esc = _assert_fp32_parity(g, o, wl["ntrees"], ctol=ctol, L=wl["L"], M=wl["M"], unpinned=wl.get("past_blowup"))
+    if name in ("var_coef_2d", "drift_2d"):
+        assert esc == []
 
 
 def test_pade_error_parity_and_calibration(grt):
